@@ -1,0 +1,636 @@
+"""CPU oracle for the companded-and-packed GEMM — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  It shares no code with the CUDA library
+(``paper_1110_5765_gb300``) and never imports it; the two meet only in the
+seeded input generators of ``synth``.
+
+What it computes, with the passage each step follows (Anastasia & Andreopoulos,
+"Throughput-Distortion Computation of Generic Matrix Multiplication"):
+
+* ``block_stats``      max|x|, sum x^2 and count per L x L block (Sec. 3, Sec. 5.B)
+* ``q_for``/``w_ef``   packing coefficient z = 2^-q and error-free packing limit
+                       (Prop. 1, eqs. 15-17)
+* ``model_noise``      quantization + representation noise power (Prop. 2 eq. 19,
+                       eq. 21) summed over all subblock products, SNR (eq. 20)
+* ``plan_*``           fixed-bit companders, or the minimum-error companders of
+                       Prop. 4 (eqs. 26-27) with the largest W meeting a target
+                       (Sec. 6), separable per-block reading
+* ``tdgemm``           compand (eq. 3), pack (eqs. 6-7 / 11), packed MAC
+                       (eqs. 8 / 12), unpack (eqs. 9-10 / 13-14), de-compand and
+                       sum over slabs (eqs. 5, 2) — the arithmetic lives in
+                       ``tdg_oracle.c`` (plain loops, fma, rint)
+* ``exact_gemm``       fp64 reference product, ``snr_db`` (eq. 20 over all of C)
+* ``tc_int_gemm``      eq. 4 on exact integers per slab (the tensor-core form)
+* ``tc_fp8_gemm``      the same with 8-bit E4M3 codes instead of integers
+
+Every function above is pinned to something outside itself (values printed
+in the paper, closed forms, library routines, brute force) in
+``tests/test_oracle_pins.py``.  The only comparison marked "parity unpinned"
+there is the loose check against the Fig. 7 end points, which the paper
+measured at another block size, size and machine.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
+SRC = os.path.join(HERE, "tdg_oracle.c")
+
+U_SAFE = 50                      # Prop. 1: "one can set u_safe = 50"
+MANTISSA_BITS = {"f32": 24, "f64": 53}   # u_sys = 2^-p, unit roundoff of T
+NP_T = {"f32": np.float32, "f64": np.float64}
+
+_lock = threading.Lock()
+_lib = None
+
+
+# --------------------------------------------------------------------------
+# building / loading the C part
+# --------------------------------------------------------------------------
+def build(force: bool = False) -> str:
+    """Compile ``tdg_oracle.c`` into ``_build/liboracle.so`` (plain gcc)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(LIB_PATH)
+            and os.path.getmtime(LIB_PATH) >= os.path.getmtime(SRC)):
+        return LIB_PATH
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            L.orc_e4m3_rn_sat.restype = ctypes.c_double
+            L.orc_e4m3_rn_sat.argtypes = [ctypes.c_double]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+# --------------------------------------------------------------------------
+# block statistics (Sec. 3: min/max per subblock; Sec. 5.B: sigma per subblock)
+# --------------------------------------------------------------------------
+@dataclass
+class BlockStats:
+    m: np.ndarray     # max |x| per block
+    e: np.ndarray     # sum of x^2 per block (fp64)
+    n: np.ndarray     # valid elements per block
+
+    @property
+    def var(self) -> np.ndarray:
+        """sigma^2 as the mean square about zero (the model's zero-mean sources)."""
+        return self.e / self.n
+
+
+def block_stats(X: np.ndarray, L: int) -> BlockStats:
+    """Per L x L block of op(X): max|x| (exact), sum x^2 accumulated as the
+    correctly rounded sum (math.fsum) of fp64 squares, and the element count."""
+    rows, cols = X.shape
+    nbr, nbc = -(-rows // L), -(-cols // L)
+    m = np.zeros((nbr, nbc))
+    e = np.zeros((nbr, nbc))
+    n = np.zeros((nbr, nbc))
+    X64 = X.astype(np.float64)
+    for i in range(nbr):
+        for j in range(nbc):
+            blk = X64[i * L:(i + 1) * L, j * L:(j + 1) * L]
+            m[i, j] = float(np.max(np.abs(blk)))
+            e[i, j] = math.fsum((blk * blk).ravel().tolist())
+            n[i, j] = blk.size
+    return BlockStats(m, e, n)
+
+
+# --------------------------------------------------------------------------
+# Prop. 1 (eqs. 15-17)
+# --------------------------------------------------------------------------
+def q_for(R: int) -> int:
+    """Smallest q with z = 2^-q <= 1 / (2 R_max + u_safe)  (eq. 15)."""
+    n = 2 * int(R) + U_SAFE
+    return (n - 1).bit_length()
+
+
+def r_cap(q: int) -> int:
+    """Largest R_max that z = 2^-q admits under eq. 15."""
+    return ((1 << q) - U_SAFE) // 2
+
+
+def w_ef(R: int, q: int, dtype: str) -> int:
+    """Eq. 16: W_ef <= floor(log_z[(2 R_max + 1) u_sys] + 1), u_sys = 2^-p."""
+    p = MANTISSA_BITS[dtype]
+    return int(math.floor(1.0 + (p - math.log2(2 * R + 1)) / q))
+
+
+def r_level(t: int) -> int:
+    """The t-th candidate R_max: floor(2^(t/4)), four levels per octave,
+    computed with exact integer square roots."""
+    return math.isqrt(math.isqrt(1 << t))
+
+
+# --------------------------------------------------------------------------
+# noise model (eqs. 19-21), summed over every subblock product (i, l, j)
+# --------------------------------------------------------------------------
+@dataclass
+class Aggregates:
+    S: float          # expected output power, L * sum sigma_A^2 sigma_B^2
+    T1: float         # sum_l (sum_i sigma_A,il^2)(sum_j m_B,lj^2)
+    T2: float         # sum_l (sum_j sigma_B,lj^2)(sum_i m_A,il^2)
+    T3: float         # sum_l (sum_i m_A,il^2)(sum_j m_B,lj^2)
+    L: int
+
+    @property
+    def rho(self) -> float:
+        """Gamma_A / Gamma_B that eq. 26 implies for the whole product."""
+        if self.T1 <= 0.0 or self.T2 <= 0.0:
+            return 1.0
+        return math.sqrt(self.T2 / self.T1)
+
+
+def aggregates(stA: BlockStats, stB: BlockStats, L: int) -> Aggregates:
+    """Per-slab sums of the block statistics, written out as plain loops."""
+    nM, nK = stA.m.shape
+    nK2, nN = stB.m.shape
+    assert nK == nK2
+    vA, vB = stA.var, stB.var
+    S = T1 = T2 = T3 = 0.0
+    for l in range(nK):
+        X = sum(float(vA[i, l]) for i in range(nM))
+        MA = sum(float(stA.m[i, l]) ** 2 for i in range(nM))
+        Y = sum(float(vB[l, j]) for j in range(nN))
+        MB = sum(float(stB.m[l, j]) ** 2 for j in range(nN))
+        S += X * Y
+        T1 += X * MB
+        T2 += Y * MA
+        T3 += MA * MB
+    return Aggregates(L * S, T1, T2, T3, L)
+
+
+def model_noise(ag: Aggregates, gA: int, gB: int, s: float) -> float:
+    """Eq. 21 summed over all (i, l, j), with c_A = Gamma_A / m_A per block:
+    L sigma_A^2 / (12 c_B^2) + L sigma_B^2 / (12 c_A^2) + L / (144 c_A^2 c_B^2)
+    + s^2 / (c_A c_B)^2."""
+    L = ag.L
+    return (L * ag.T1 / (12.0 * gB * gB) + L * ag.T2 / (12.0 * gA * gA)
+            + ag.T3 * (L / 144.0 + s * s) / (float(gA) * gA * float(gB) * gB))
+
+
+def model_snr_db(ag: Aggregates, gA: int, gB: int, s: float) -> float:
+    """Eq. 20 with the noise of ``model_noise``."""
+    N = model_noise(ag, gA, gB, s)
+    if N <= 0.0:
+        return math.inf
+    return 10.0 * math.log10(ag.S / N)
+
+
+# --------------------------------------------------------------------------
+# planning (Prop. 4, Sec. 6)
+# --------------------------------------------------------------------------
+@dataclass
+class Plan:
+    W: int                    # packing used (1 = conventional GEMM, no companding)
+    q: int = 0
+    gA: int = 0
+    gB: int = 0
+    R: int = 0
+    Wef: int = 0
+    t: int = -1               # R level index in target mode
+    pred_snr_db: float = math.nan
+    status: str = "ok"        # "ok" | "unreachable"
+    manual_c: tuple | None = None
+    extra: dict = field(default_factory=dict)
+
+
+class STable:
+    """Representation-noise RMSE s(R_max, W) per R level (Sec. 4.B, eq. 18):
+    ``s[(dtype, form, W, L)][t]``."""
+
+    def __init__(self, data: dict | None = None):
+        self.data = data or {}
+
+    @staticmethod
+    def key(dtype, form, W, L):
+        return f"{dtype}/{form}/W{W}/L{L}"
+
+    def get(self, dtype, form, W, L, t):
+        d = self.data.get(self.key(dtype, form, W, L))
+        if d is None:
+            return None
+        v = d.get(str(t))
+        return None if v is None else float(v["s"])
+
+
+def rep_noise(st: STable | None, dtype, form, W, L, t, R, q) -> float | None:
+    """s for a candidate: 0 inside the error-free region of Prop. 1, else the
+    calibrated value (None: not calibrated, candidate not usable)."""
+    if W <= w_ef(R, q, dtype):
+        return 0.0
+    if st is None:
+        return None
+    return st.get(dtype, form, W, L, t)
+
+
+def split_gammas(R: int, L: int, rho: float) -> tuple[int, int]:
+    """Integer companders for a budget R_max (eq. 17: R = L Gamma_A Gamma_B)
+    split in the ratio of eq. 26: Gamma_A = floor(sqrt(G rho)), G = R / L."""
+    G = R // L
+    if G < 1:
+        return 0, 0
+    gA = int(math.floor(math.sqrt((R / L) * rho)))
+    gA = max(1, min(gA, G))
+    gB = max(1, R // (L * gA))
+    return gA, gB
+
+
+T_MAX = {"f32": 4 * 24, "f64": 4 * 40}
+
+
+def plan_fixed(bits: int, L: int, W: int, dtype: str, form: str,
+               ag: Aggregates | None = None, st: STable | None = None) -> Plan:
+    """Fixed-bit companding: Gamma_A = Gamma_B = 2^(bits-1) - 1, R_max by eq. 17,
+    z by eq. 15, the requested W."""
+    g = (1 << (bits - 1)) - 1
+    R = L * g * g
+    q = q_for(R)
+    pl = Plan(W=W, q=q, gA=g, gB=g, R=R, Wef=w_ef(R, q, dtype))
+    if ag is not None:
+        if W <= pl.Wef:
+            s = 0.0
+        else:
+            s = None
+            if st is not None:
+                t = max(t for t in range(T_MAX[dtype] + 1) if r_level(t) <= R)
+                s = st.get(dtype, form, W, L, t)
+        pl.pred_snr_db = model_snr_db(ag, g, g, s) if s is not None else math.nan
+    return pl
+
+
+def plan_target(ag: Aggregates, L: int, Wreq: int, dtype: str, form: str,
+                target_db: float, st: STable | None, allow_fallback: bool = True) -> Plan:
+    """Distortion-controlled choice (Prop. 4 and Sec. 6, uniform W per call):
+    for W = Wreq, Wreq-1, ..., 2 take the R_max level maximising the model SNR
+    (eq. 27's argmax, ties to the smaller level) with companders split per
+    eq. 26; keep the first W whose best SNR meets the target.  Otherwise the
+    conventional product (W = 1) or 'unreachable'."""
+    t_lo = 4 * (L.bit_length() - 1)          # smallest level with R >= L
+    while r_level(t_lo) < L:
+        t_lo += 1
+    best_overall = None
+    for W in range(Wreq, 1, -1):
+        best = None
+        for t in range(t_lo, T_MAX[dtype] + 1):
+            R_t = r_level(t)
+            q = q_for(R_t)
+            gA, gB = split_gammas(R_t, L, ag.rho)
+            if gA < 1:
+                continue
+            R = L * gA * gB
+            s = rep_noise(st, dtype, form, W, L, t, R, q)
+            if s is None:
+                continue
+            snr = model_snr_db(ag, gA, gB, s)
+            if best is None or snr > best.pred_snr_db:
+                best = Plan(W=W, q=q, gA=gA, gB=gB, R=R, Wef=w_ef(R, q, dtype), t=t,
+                            pred_snr_db=snr)
+        if best is None:
+            continue
+        if best_overall is None:
+            best_overall = best
+        if best.pred_snr_db >= target_db:
+            return best
+    if allow_fallback:
+        return Plan(W=1, pred_snr_db=math.inf)
+    pl = best_overall or Plan(W=Wreq)
+    pl.status = "unreachable"
+    return pl
+
+
+def compander(m: np.ndarray, gamma: int) -> tuple[np.ndarray, np.ndarray]:
+    """c = Gamma / max|x| per block (so |a~| <= Gamma, eq. 17) and s = 1/c, both
+    fp64; an all-zero block gets c = s = 0."""
+    c = np.zeros_like(m)
+    s = np.zeros_like(m)
+    nz = m > 0
+    c[nz] = float(gamma) / m[nz]
+    s[nz] = 1.0 / c[nz]
+    return c, s
+
+
+# --------------------------------------------------------------------------
+# the companded-and-packed product
+# --------------------------------------------------------------------------
+def compand(X: np.ndarray, L: int, c: np.ndarray, dtype: str) -> np.ndarray:
+    """Eq. 3 per block; X is op(X), c the per-block fp64 companders."""
+    T = NP_T[dtype]
+    X = np.ascontiguousarray(X, dtype=T)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    out = np.empty_like(X)
+    fn = getattr(lib(), f"orc_compand_{dtype}")
+    fn(_p(X), _i64(X.shape[0]), _i64(X.shape[1]), _int(L), _p(c), _p(out))
+    return out
+
+
+def pack_cols(Xq: np.ndarray, L: int, W: int, w: float, dtype: str) -> np.ndarray:
+    """Eq. 6 (w = z) / eq. 7 applied to a transpose: digits along columns."""
+    T = NP_T[dtype]
+    Xq = np.ascontiguousarray(Xq, dtype=T)
+    rows, cols = Xq.shape
+    P = -(-L // W)
+    out = np.empty((rows, -(-cols // L) * P), dtype=T)
+    fn = getattr(lib(), f"orc_pack_cols_{dtype}")
+    wt = ctypes.c_float(w) if dtype == "f32" else ctypes.c_double(w)
+    fn(_p(Xq), _i64(rows), _i64(cols), _int(L), _int(W), wt, _p(out))
+    return out
+
+
+def pack_rows(Xq: np.ndarray, L: int, W: int, w: float, dtype: str) -> np.ndarray:
+    """Eq. 7 (w = z^-1) and eq. 11 (w = z): digits along rows."""
+    T = NP_T[dtype]
+    Xq = np.ascontiguousarray(Xq, dtype=T)
+    rows, cols = Xq.shape
+    P = -(-L // W)
+    out = np.empty((-(-rows // L) * P, cols), dtype=T)
+    fn = getattr(lib(), f"orc_pack_rows_{dtype}")
+    wt = ctypes.c_float(w) if dtype == "f32" else ctypes.c_double(w)
+    fn(_p(Xq), _i64(rows), _i64(cols), _int(L), _int(W), wt, _p(out))
+    return out
+
+
+def _window(rows, cols, M, N):
+    r0, r1 = (0, M) if rows is None else rows
+    c0, c1 = (0, N) if cols is None else cols
+    return int(r0), int(r1), int(c0), int(c1)
+
+
+def epilogue(Cacc: np.ndarray, alpha: float, beta: float, Cin: np.ndarray | None,
+             dtype: str) -> np.ndarray:
+    """C = alpha * Cacc + beta * C_in (C_in not read when beta == 0)."""
+    T = NP_T[dtype]
+    Cacc = np.ascontiguousarray(Cacc, dtype=T)
+    Cin = np.zeros_like(Cacc) if Cin is None else np.ascontiguousarray(Cin, dtype=T)
+    out = np.empty_like(Cacc)
+    fn = getattr(lib(), f"orc_epilogue_{dtype}")
+    fn(_p(Cacc), _p(Cin), _i64(Cacc.size), ctypes.c_double(alpha), ctypes.c_double(beta),
+       _p(out))
+    return out
+
+
+def gemm_plain(A: np.ndarray, B: np.ndarray, dtype: str, rows=None, cols=None) -> np.ndarray:
+    """Conventional product in T: fma chain over ascending k from +0."""
+    T = NP_T[dtype]
+    A = np.ascontiguousarray(A, dtype=T)
+    B = np.ascontiguousarray(B, dtype=T)
+    M, K = A.shape
+    N = B.shape[1]
+    r0, r1, c0, c1 = _window(rows, cols, M, N)
+    out = np.empty((r1 - r0, c1 - c0), dtype=T)
+    fn = getattr(lib(), f"orc_gemm_{dtype}")
+    fn(_p(A), _p(B), _i64(M), _i64(N), _i64(K), _i64(r0), _i64(r1), _i64(c0), _i64(c1),
+       _p(out))
+    return out
+
+
+def exact_gemm(A: np.ndarray, B: np.ndarray, rows=None, cols=None) -> np.ndarray:
+    """Reference product R = AB in fp64 (the 'native precision' of eq. 20)."""
+    return gemm_plain(A.astype(np.float64), B.astype(np.float64), "f64", rows, cols)
+
+
+def snr_db(C: np.ndarray, Cref: np.ndarray) -> float:
+    """Eq. 20 measured: 10 log10( sum Cref^2 / sum (C - Cref)^2 ) in fp64."""
+    C = C.astype(np.float64)
+    Cref = Cref.astype(np.float64)
+    sig = math.fsum((Cref * Cref).ravel().tolist())
+    err = C - Cref
+    noise = math.fsum((err * err).ravel().tolist())
+    if noise == 0.0:
+        return math.inf
+    return 10.0 * math.log10(sig / noise)
+
+
+@dataclass
+class Result:
+    C: np.ndarray
+    plan: Plan
+    rint: np.ndarray | None = None
+    cA: np.ndarray | None = None
+    cB: np.ndarray | None = None
+    sA: np.ndarray | None = None
+    sB: np.ndarray | None = None
+    Abar: np.ndarray | None = None
+    Bbar: np.ndarray | None = None
+
+
+def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: str,
+           bits: int = 0, target_db: float = math.nan, s_table: STable | None = None,
+           allow_fallback: bool = True, manual: tuple | None = None,
+           gammas: tuple | None = None, alpha: float = 1.0, beta: float = 0.0, C_in: np.ndarray | None = None,
+           rows=None, cols=None, want_rint: bool = False, keep_packed: bool = False) -> Result:
+    """Companded-and-packed C = alpha op(A) op(B) + beta C on the CPU.
+
+    A is op(A) (M x K), B is op(B) (K x N), both already in T.  ``form`` is
+    'sym' (eqs. 6-10), 'asym' (eqs. 11-14) or 'plain' (no companding, W = 1).
+    Parameters come from ``bits`` (fixed-bit mode), ``target_db`` (distortion
+    target) or ``manual = (q, c_A, c_B)`` (uniform companders, as in the
+    measurement protocol of Sec. 4.B) or ``gammas = (Gamma_A, Gamma_B)``
+    (given integer companders).  ``rows``/``cols`` restrict the computed
+    outputs to a window (for asym, row windows must align to L)."""
+    T = NP_T[dtype]
+    A = np.ascontiguousarray(A, dtype=T)
+    B = np.ascontiguousarray(B, dtype=T)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    r0, r1, c0, c1 = _window(rows, cols, M, N)
+    nM, nK, nN = -(-M // L), -(-K // L), -(-N // L)
+
+    if form == "plain":
+        C = gemm_plain(A, B, dtype, (r0, r1), (c0, c1))
+        Cin = None if C_in is None else C_in[r0:r1, c0:c1]
+        return Result(epilogue(C, alpha, beta, Cin, dtype), Plan(W=1))
+
+    if manual is not None:
+        q, cAv, cBv = manual
+        pl = Plan(W=W, q=int(q), manual_c=(cAv, cBv))
+        cA = np.full((nM, nK), float(cAv))
+        cB = np.full((nK, nN), float(cBv))
+        sA = np.where(cA > 0, 1.0 / np.where(cA > 0, cA, 1.0), 0.0)
+        sB = np.where(cB > 0, 1.0 / np.where(cB > 0, cB, 1.0), 0.0)
+    else:
+        stA = block_stats(A, L)
+        stB = block_stats(B, L)
+        ag = aggregates(stA, stB, L)
+        if gammas is not None:
+            gA, gB = int(gammas[0]), int(gammas[1])
+            R = L * gA * gB
+            q = q_for(R)
+            pl = Plan(W=W, q=q, gA=gA, gB=gB, R=R, Wef=w_ef(R, q, dtype))
+            pl.pred_snr_db = model_snr_db(ag, gA, gB, 0.0) if W <= pl.Wef else math.nan
+        elif bits > 0:
+            pl = plan_fixed(bits, L, W, dtype, form, ag, s_table)
+        else:
+            pl = plan_target(ag, L, W, dtype, form, target_db, s_table, allow_fallback)
+        if pl.W == 1 and pl.gA == 0:
+            C = gemm_plain(A, B, dtype, (r0, r1), (c0, c1))
+            Cin = None if C_in is None else C_in[r0:r1, c0:c1]
+            return Result(epilogue(C, alpha, beta, Cin, dtype), pl)
+        cA, sA = compander(stA.m, pl.gA)
+        cB, sB = compander(stB.m, pl.gB)
+
+    Aq = compand(A, L, cA, dtype)
+    Bq = compand(B, L, cB, dtype)
+    Wu = pl.W
+    P = -(-L // Wu)
+    z = math.ldexp(1.0, -pl.q)
+    Q = math.ldexp(1.0, pl.q)
+    shape = (r1 - r0, c1 - c0)
+    Cacc = np.empty(shape, dtype=T)
+    rint = np.empty(shape + (nK,), dtype=np.int64) if want_rint else None
+    rint_p = _p(rint) if want_rint else ctypes.c_void_p(0)
+    sA = np.ascontiguousarray(sA, dtype=np.float64)
+    sB = np.ascontiguousarray(sB, dtype=np.float64)
+    if form == "sym":
+        Abar = pack_cols(Aq, L, Wu, z, dtype)                 # eq. 6
+        Bbar = np.ascontiguousarray(pack_cols(np.ascontiguousarray(Bq.T), L, Wu, Q, dtype).T)  # eq. 7
+        fn = getattr(lib(), f"orc_sym_gemm_{dtype}")
+        fn(_p(Abar), _p(Bbar), _i64(M), _i64(N), _i64(nK), _int(P), _int(L), _int(pl.q),
+           _p(sA), _p(sB), _i64(r0), _i64(r1), _i64(c0), _i64(c1), rint_p, _p(Cacc))
+    elif form == "asym":
+        assert r0 % L == 0 and (r1 % L == 0 or r1 == M)
+        Abar = pack_rows(Aq, L, Wu, z, dtype)                 # eq. 11
+        Bbar = Bq
+        fn = getattr(lib(), f"orc_asym_gemm_{dtype}")
+        fn(_p(Abar), _p(Bq), _i64(M), _i64(N), _i64(K), _int(P), _int(L), _int(Wu),
+           _int(pl.q), _p(sA), _p(sB), _i64(r0), _i64(r1), _i64(c0), _i64(c1), rint_p,
+           _p(Cacc))
+    else:
+        raise ValueError(form)
+    Cin = None if C_in is None else C_in[r0:r1, c0:c1]
+    C = epilogue(Cacc, alpha, beta, Cin, dtype)
+    res = Result(C, pl, rint, cA, cB, sA, sB)
+    if keep_packed:
+        res.Abar, res.Bbar = Abar, Bbar
+    return res
+
+
+# --------------------------------------------------------------------------
+# quantized tensor-core forms
+# --------------------------------------------------------------------------
+TC_INT_EXACT_LIMIT = (1 << 24) - 1      # per-slab |sum| that fp32 holds exactly
+TC_INT_MAX_GAMMA = 2048                 # integers that a 16-bit float holds exactly
+
+
+def tc_int_gammas(L: int, ag: Aggregates | None, bits: int) -> tuple[int, int]:
+    """Fixed bits: Gamma = 2^(bits-1) - 1.  Otherwise the largest companders
+    with L Gamma_A Gamma_B <= 2^24 - 1 (every per-slab sum exact in fp32, so the
+    fp32 accumulation equals eq. 4 in integers) split per eq. 26."""
+    if bits > 0:
+        g = (1 << (bits - 1)) - 1
+        return g, g
+    rho = ag.rho if ag is not None else 1.0
+    gA, gB = split_gammas(TC_INT_EXACT_LIMIT, L, rho)
+    gA = min(gA, TC_INT_MAX_GAMMA)
+    gB = min(gB, TC_INT_MAX_GAMMA, TC_INT_EXACT_LIMIT // (L * gA))
+    return gA, gB
+
+
+def tc_int_gemm(A: np.ndarray, B: np.ndarray, *, L: int, bits: int = 0,
+                rows=None, cols=None, want_rint: bool = False) -> Result:
+    """Companded integer GEMM (eqs. 3, 4, 5, 2) with exact per-slab integer sums,
+    fp32 companding and fp32 de-companding (the tensor-core precision form)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    M, K = A.shape
+    N = B.shape[1]
+    L = int(L)
+    stA, stB = block_stats(A, L), block_stats(B, L)
+    ag = aggregates(stA, stB, L)
+    gA, gB = tc_int_gammas(L, ag, bits)
+    cA, sA = compander(stA.m, gA)
+    cB, sB = compander(stB.m, gB)
+    Aq = compand(A, L, cA, "f32")
+    Bq = compand(B, L, cB, "f32")
+    r0, r1, c0, c1 = _window(rows, cols, M, N)
+    nK = -(-K // L)
+    Cacc = np.empty((r1 - r0, c1 - c0), dtype=np.float32)
+    rint = np.empty((r1 - r0, c1 - c0, nK), dtype=np.int64) if want_rint else None
+    lib().orc_int_gemm_f32(_p(Aq), _p(Bq), _i64(M), _i64(N), _i64(K), _int(L), _p(sA),
+                           _p(sB), _i64(r0), _i64(r1), _i64(c0), _i64(c1),
+                           _p(rint) if want_rint else ctypes.c_void_p(0), _p(Cacc))
+    pl = Plan(W=1, gA=gA, gB=gB, R=L * gA * gB, pred_snr_db=model_snr_db(ag, gA, gB, 0.0))
+    return Result(Cacc, pl, rint, cA, cB, sA, sB)
+
+
+FP8_MAX = 448.0
+
+
+def e4m3(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest E4M3 value (ties to even, saturating at 448)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    lib().orc_e4m3_array(_p(x), _i64(x.size), _p(out))
+    return out
+
+
+def tc_fp8_gemm(A: np.ndarray, B: np.ndarray, *, L: int, rows=None, cols=None) -> Result:
+    """8-bit float form: a~ = e4m3(fl32(a c)) with c = 448 / max|A_il| per block,
+    per-slab sums exact, rounded once to fp32, de-companded in fp32."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    M, K = A.shape
+    N = B.shape[1]
+    stA, stB = block_stats(A, L), block_stats(B, L)
+    cA = np.zeros_like(stA.m)
+    cB = np.zeros_like(stB.m)
+    cA[stA.m > 0] = FP8_MAX / stA.m[stA.m > 0]
+    cB[stB.m > 0] = FP8_MAX / stB.m[stB.m > 0]
+    sA = np.where(cA > 0, 1.0 / np.where(cA > 0, cA, 1.0), 0.0)
+    sB = np.where(cB > 0, 1.0 / np.where(cB > 0, cB, 1.0), 0.0)
+
+    def enc(X, c):
+        nbc = c.shape[1]
+        cT = np.repeat(np.repeat(c.astype(np.float32), L, 0), L, 1)[:X.shape[0], :X.shape[1]]
+        del nbc
+        return e4m3((X * cT).astype(np.float64))        # product rounded in fp32
+
+    Aq, Bq = enc(A, cA), enc(B, cB)
+    r0, r1, c0, c1 = _window(rows, cols, M, N)
+    Cacc = np.empty((r1 - r0, c1 - c0), dtype=np.float32)
+    lib().orc_fp8_gemm_f32(_p(Aq), _p(Bq), _i64(M), _i64(N), _i64(K), _int(L), _p(sA),
+                           _p(sB), _i64(r0), _i64(r1), _i64(c0), _i64(c1), _p(Cacc))
+    return Result(Cacc, Plan(W=1), None, cA, cB, sA, sB)
+
+
+def r_max_eq17(L: int, maxA: float, maxB: float, cA: float = 1.0, cB: float = 1.0) -> int:
+    """Eq. 17 as printed: R_max = [[c_A c_B L max|A| max|B|]]."""
+    return int(round(cA * cB * L * maxA * maxB))
+
+
+def load_s_table(path: str | None = None) -> STable:
+    import json
+    path = path or os.path.join(HERE, "s_table.json")
+    if not os.path.exists(path):
+        return STable({})
+    with open(path) as f:
+        return STable(json.load(f)["tables"])
