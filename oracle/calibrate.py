@@ -5,7 +5,7 @@ the oracle's planner reads.  It calls nothing but ``oracle`` and ``synth``.
 
 Protocol (Sec. 4.B, adapted to a ladder of R_max levels):
   for every working type, packing form, W in {2,3,4} and block size L,
-  for every level t with R_t = floor(2^(t/4)) >= L:
+  for every level t with R_t = floor(2^(t//4) (4 + t%4) / 4) >= L:
     z = 2^-q with the smallest q meeting eq. 15 for R_t,
     Gamma_A = min(22, R_t // L)   (the paper keeps max|A| = 22),
     Gamma_B = R_t // (L Gamma_A)  (the paper sweeps max|B|),
@@ -85,7 +85,7 @@ def main(argv=None):
     doc = {
         "what": "representation-noise RMSE s(R_max, W) on the oracle's arithmetic",
         "protocol": "Sec. 4.B: c_A=c_B=1, integer inputs, max|A|=22, five instantiations",
-        "levels": "R_t = floor(2^(t/4)); z = 2^-q, smallest q with 2^q >= 2 R_t + 50",
+        "levels": "R_t = floor(2^(t//4) (4 + t%4) / 4); z = 2^-q, smallest q with 2^q >= 2 R_t + 50",
         "tables": tables,
     }
     with open(args.out, "w") as f:

@@ -145,9 +145,10 @@ def w_ef(R: int, q: int, dtype: str) -> int:
 
 
 def r_level(t: int) -> int:
-    """The t-th candidate R_max: floor(2^(t/4)), four levels per octave,
-    computed with exact integer square roots."""
-    return math.isqrt(math.isqrt(1 << t))
+    """The t-th candidate R_max: floor(2^a (4 + f) / 4) with a = t // 4 and
+    f = t % 4, i.e. four levels per octave at 1, 1.25, 1.5 and 1.75 times 2^a."""
+    a, f = divmod(int(t), 4)
+    return ((4 + f) << a) // 4
 
 
 # --------------------------------------------------------------------------
