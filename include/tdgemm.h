@@ -1,0 +1,208 @@
+/*
+ * tdgemm — throughput-distortion GEMM on one GB300 (sm_103a).
+ *
+ * C ABI of the companded-and-packed matrix product of Anastasia &
+ * Andreopoulos, "Throughput-Distortion Computation of Generic Matrix
+ * Multiplication" (the paper):
+ *
+ *     C = alpha * op(A) * op(B) + beta * C,   op(A): M x K,  op(B): K x N
+ *
+ * computed through four steps on the device:
+ *   (a) per L x L block statistics and companders, then companding and
+ *       rounding of every input element                      (Sec. 3.A, eq. 3,
+ *                                                              Sec. 5, eqs. 15-27)
+ *   (b) packing W quantized values into one floating-point number
+ *       (symmetric form, eqs. 6-7; asymmetric form, eq. 11)
+ *   (c) the packed multiply-accumulate, W results per FMA  (eqs. 8, 12)
+ *   (d) unpacking, de-companding and rescaling              (eqs. 9-10, 13-14, 5, 2)
+ * plus a tensor-core form of (c) on the companded integers (the integer
+ * processing of Remark 1, on 16-bit float carriers) and on 8-bit E4M3 codes.
+ *
+ * Conventions (all entry points):
+ *   - Matrices are row-major.  op(X) = X for trans 'N'/'n', X^T for 'T'/'t'.
+ *     lda, ldb, ldc are leading dimensions in elements of the stored matrix.
+ *   - A, B, C are device pointers owned by the caller; they must stay valid
+ *     until the work queued on `stream` has finished.  `stream` is a
+ *     cudaStream_t (NULL = the legacy default stream).
+ *   - The plan owns every other device buffer (statistics, companders, packed
+ *     operands) and frees it in tdgemm_plan_destroy.
+ *   - All device work is queued on `stream`; no entry point synchronises the
+ *     host except tdgemm_plan_info, tdgemm_unpack (when given host buffers)
+ *     and tdgemm_run_host.
+ *   - Argument errors are returned at once and leave the plan unchanged.
+ *     Conditions found on the device (non-finite input, unreachable target)
+ *     are written to a device status word that tdgemm_plan_info reads.
+ *   - A plan is not thread-safe; distinct plans are independent.
+ *   - Every failing call records a message readable with tdgemm_last_error()
+ *     (thread-local).
+ */
+#ifndef TDGEMM_H
+#define TDGEMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdgemm_plan_s *tdgemm_plan_t;
+
+/* Working type T of the packed arithmetic (Sec. 7: sGEMM / dGEMM). */
+typedef enum { TDG_F32 = 0, TDG_F64 = 1 } tdg_dtype;
+
+/* Form of step (c):
+ *   TDG_PLAIN   conventional product in T, no companding (W = 1, Sec. 7 "plain")
+ *   TDG_SYM     symmetric packing, eqs. 6-10
+ *   TDG_ASYM    asymmetric packing, eqs. 11-14
+ *   TDG_TC_INT  companded integers (eq. 3) multiplied on tensor cores as
+ *               integer-valued fp16 operands; every per-slab sum is an integer
+ *               below 2^24, so the fp32 accumulation equals eq. 4 exactly
+ *               (Remark 1's integer processing).  fp32 inputs only.
+ *   TDG_TC_FP8  per-block companded E4M3 codes (c = 448 / max|x|) on tensor
+ *               cores with fp32 accumulation.  fp32 inputs only.            */
+typedef enum {
+    TDG_PLAIN = 0,
+    TDG_SYM = 1,
+    TDG_ASYM = 2,
+    TDG_TC_INT = 3,
+    TDG_TC_FP8 = 4
+} tdg_form;
+
+typedef enum {
+    TDG_OK = 0,
+    TDG_EINVAL = 1,          /* bad argument                                   */
+    TDG_ENOMEM = 2,          /* device allocation failed                       */
+    TDG_ECUDA = 3,           /* a CUDA call failed (message in last_error)     */
+    TDG_EUNSUPPORTED = 4,    /* valid but not built (e.g. TC form with f64)    */
+    TDG_EUNREACHABLE = 5,    /* target SNR not met at any W > 1, no fallback   */
+    TDG_ETIMEOUT = 6,        /* a device wait exceeded its iteration budget    */
+    TDG_ENONFINITE = 7,      /* NaN or Inf found in an input block             */
+    TDG_ESTATE = 8           /* call out of order (e.g. gemm before pack)      */
+} tdg_status;
+
+/* flags for tdgemm_plan */
+#define TDG_ALLOW_FALLBACK 0x1u  /* target unmet at every W > 1: compute the plain
+                                    product (W = 1, Sec. 6) instead of failing  */
+#define TDG_KEEP_PACKED    0x2u  /* tdgemm_gemm also stores every packed slab
+                                    result r_bar for tdgemm_unpack              */
+
+/* What the planner chose, read back by tdgemm_plan_info (synchronises). */
+typedef struct {
+    int32_t W_used;          /* packing used; 1 = plain product                 */
+    int32_t q;               /* z = 2^-q (eq. 15)                               */
+    int32_t gamma_a;         /* |a~| <= gamma_a, c_A = gamma_a / max|A_il|      */
+    int32_t gamma_b;
+    int64_t r_max;           /* L * gamma_a * gamma_b (eq. 17)                  */
+    int32_t w_ef;            /* error-free packing limit for r_max (eq. 16)     */
+    int32_t level;           /* R_max candidate index in target mode, else -1   */
+    double pred_snr_db;      /* model SNR, eqs. 19-21 (NaN if not modelled)     */
+    int64_t workspace_bytes; /* device memory the plan owns                     */
+    int32_t device_status;   /* tdg_status found on the device by the last pack */
+    int32_t carrier;         /* TC forms: 16 = fp16 integer carrier, 8 = e4m3   */
+} tdgemm_info;
+
+/*
+ * Create a plan: shapes, block size and packing as the paper poses the
+ * problem (Sec. 2: M x K by K x N split into L x L subblocks; eq. 1 block
+ * size; W packings; Sec. 6 distortion target).
+ *
+ *   transA, transB  'N' or 'T'
+ *   M, N, K         >= 1
+ *   lda, ldb, ldc   leading dimensions (elements) of the stored A, B, C
+ *   L               block size, a multiple of 16 in [16, 1024]; the TC forms
+ *                   need a multiple of 64
+ *   W               packing factor 1..4 (SYM, ASYM); PLAIN and TC forms: 1
+ *   dtype, form     see above
+ *   target_snr_db   distortion target in dB (used when bits == 0)
+ *   bits            > 0: fixed-bit companding, gamma = 2^(bits-1) - 1, W as
+ *                   given (bits in 2..12; TC_INT up to 12)
+ *   flags           TDG_ALLOW_FALLBACK | TDG_KEEP_PACKED
+ *
+ * On success *plan receives a new plan holding all device workspace for these
+ * shapes (allocated on the current device).  On error *plan is left NULL.
+ */
+tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB, int64_t M, int64_t N,
+                       int64_t K, int64_t lda, int64_t ldb, int64_t ldc, int L, int W,
+                       tdg_dtype dtype, tdg_form form, double target_snr_db, int bits,
+                       uint32_t flags);
+
+/*
+ * Give the planner the measured representation-noise RMSE s(R_max, W) of
+ * Sec. 4.B / eq. 18 for packing W of this plan's dtype, form and L:
+ * s[i] belongs to the R_max level t0 + i, where level t means
+ * R_t = floor(2^(t/4|0) * (4 + t%4) / 4); a negative entry marks a level that
+ * was not measured.  Host array, copied.  Without a table the planner uses
+ * only levels inside the error-free region of Prop. 1 (s = 0).
+ */
+tdg_status tdgemm_set_rep_noise(tdgemm_plan_t plan, int W, const double *s, int t0, int n);
+
+/*
+ * Manual parameters, bypassing the planner (the measurement protocol of
+ * Sec. 4.B uses c_A = c_B = 1): every block gets compander c_A (c_B) and the
+ * packing coefficient is z = 2^-q.  q in 1..60, c > 0.
+ */
+tdg_status tdgemm_set_manual(tdgemm_plan_t plan, int q, double c_a, double c_b);
+
+/*
+ * Steps (a) and (b): block statistics, planner, companders, companding and
+ * packing of A and B into the plan's workspace.  A and B are device pointers
+ * in the plan's dtype (fp32 for the TC forms).
+ */
+tdg_status tdgemm_quantize_pack(tdgemm_plan_t plan, const void *A, const void *B,
+                                void *stream);
+
+/*
+ * Steps (c) and (d): packed multiply-accumulate with unpacking,
+ * de-companding and the sum over slabs fused into the accumulator
+ * registers, then C = alpha * C_acc + beta * C (C not read when beta == 0).
+ * Requires a preceding tdgemm_quantize_pack on the same plan.
+ */
+tdg_status tdgemm_gemm(tdgemm_plan_t plan, void *C, double alpha, double beta, void *stream);
+
+/* tdgemm_quantize_pack followed by tdgemm_gemm. */
+tdg_status tdgemm_run(tdgemm_plan_t plan, const void *A, const void *B, void *C, double alpha,
+                      double beta, void *stream);
+
+/*
+ * The same with HOST buffers: A, B and C are host pointers (pinned memory
+ * gives asynchronous copies); the plan copies A and B to device staging
+ * buffers it owns, runs, copies C back and synchronises `stream`.
+ */
+tdg_status tdgemm_run_host(tdgemm_plan_t plan, const void *A, const void *B, void *C,
+                           double alpha, double beta, void *stream);
+
+/*
+ * Unfused step (d) for checking the integer domain: needs TDG_KEEP_PACKED and
+ * a preceding tdgemm_gemm.  rint_out (device, nullable) receives the unpacked
+ * integers r~ of every output and slab as int64, layout [m][n][l]
+ * (M x N x ceil(K/L)); C (device, nullable, ldc) receives the de-companded
+ * sum over slabs (alpha = 1, beta = 0).  SYM and ASYM forms only.
+ */
+tdg_status tdgemm_unpack(tdgemm_plan_t plan, int64_t *rint_out, void *C, void *stream);
+
+/* Read what the planner chose (synchronises the plan's last stream). */
+tdg_status tdgemm_plan_info(tdgemm_plan_t plan, tdgemm_info *out);
+
+/* Free the plan and its workspace (synchronises the device first). */
+tdg_status tdgemm_plan_destroy(tdgemm_plan_t plan);
+
+/*
+ * Output distortion against a reference (eq. 20 measured): accumulates
+ * sum(ref^2), sum((C - ref)^2), sum(C - ref) in fp64 over the M x N outputs
+ * into out3[0..2] (device pointer, overwritten).  C is in `dtype` with
+ * leading dimension ldc; ref is fp64 with leading dimension ldr.
+ */
+tdg_status tdgemm_snr(const void *C, int64_t ldc, tdg_dtype dtype, const double *ref,
+                      int64_t ldr, int64_t M, int64_t N, double *out3, void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *tdgemm_last_error(void);
+
+/* Library version string. */
+const char *tdgemm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDGEMM_H */

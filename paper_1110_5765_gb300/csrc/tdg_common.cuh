@@ -1,0 +1,167 @@
+// Shared device-side definitions of the tdgemm CUDA library (sm_103a).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tdgemm.h"
+
+namespace tdg {
+
+constexpr int kUSafe = 50;             // Prop. 1: u_safe = 50
+constexpr int kMaxW = 4;               // packings built: W in 1..4
+constexpr int kMaxLevels = 192;        // R_max candidate levels t in [0, 192)
+constexpr double kTcIntExact = 16777215.0;  // per-slab |sum| that fp32 holds exactly
+constexpr int kTcIntMaxGamma = 2048;        // integers exactly representable in fp16
+constexpr double kFp8Max = 448.0;           // largest finite E4M3 value
+
+enum Mode { MODE_FIXED = 0, MODE_TARGET = 1, MODE_MANUAL = 2 };
+
+// What the planner decided; written by the planner kernel in device memory,
+// read by every later kernel of the same plan (no host round trip).
+struct DevPlan {
+    int W;             // packing used (1 = plain product)
+    int q;             // z = 2^-q
+    int gA, gB;        // integer companders (gamma)
+    long long R;       // L * gA * gB
+    int Wef;           // eq. 16
+    int level;         // chosen R_max level (target mode), -1 otherwise
+    int status;        // tdg_status raised on the device (0 = ok)
+    int nonfinite;     // set by the statistics kernel
+    double pred_snr;   // model SNR (dB), NaN if not modelled
+    double S, T1, T2, T3;  // noise-model aggregates
+};
+
+// Planner inputs that do not change between calls.
+struct PlanParams {
+    int mode;          // Mode
+    int form;          // tdg_form
+    int dtype;         // tdg_dtype
+    int L, Wreq;
+    int p;             // mantissa bits of T (24 / 53): u_sys = 2^-p
+    int bits;          // fixed-bit mode
+    int allow_fallback;
+    double target_db;
+    int manual_q;
+    double manual_cA, manual_cB;
+    int nM, nK, nN;    // block counts
+    long long M, N, K;
+    int t0, nt;        // rep-noise table levels [t0, t0 + nt)
+};
+
+// ---------------------------------------------------------------------------
+// small integer helpers shared by planner kernels
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int cdiv_i(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// R_max level t: floor(2^(t div 4) * (4 + t mod 4) / 4)
+__host__ __device__ inline long long r_level(int t) {
+    return ((long long)(4 + (t & 3)) << (t >> 2)) >> 2;
+}
+
+// number of bits of a positive integer
+__host__ __device__ inline int bit_length(unsigned long long v) {
+#ifdef __CUDA_ARCH__
+    return v ? 64 - __clzll((long long)v) : 0;
+#else
+    return v ? 64 - __builtin_clzll(v) : 0;
+#endif
+}
+
+// eq. 15: smallest q with 2^q >= 2 R + u_safe
+__host__ __device__ inline int q_for(long long R) {
+    return bit_length((unsigned long long)(2 * R + kUSafe - 1));
+}
+
+// eq. 16 in integers: W_ef = 1 + floor((p - bitlen(2R + 1)) / q); for R >= 1
+// 2R + 1 is odd and above 1, so log2(2R + 1) lies strictly inside
+// (bitlen - 1, bitlen) and the floor equals that of the logarithmic form.
+__host__ __device__ inline int w_ef(long long R, int q, int p) {
+    int b = bit_length((unsigned long long)(2 * R + 1));
+    int num = p - b;
+    int fl = num >= 0 ? num / q : -((-num + q - 1) / q);
+    return 1 + fl;
+}
+
+// ---------------------------------------------------------------------------
+// PTX helpers: shared-memory addresses, mbarriers, TMA
+// ---------------------------------------------------------------------------
+__device__ inline uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ inline void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ inline void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ inline void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ inline void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ inline void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after `budget_ns` nanoseconds
+// of the global timer and returns false.
+__device__ inline uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kWaitBudgetNs = 2000000000ull;   // 2 s
+
+__device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t start = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - start > kWaitBudgetNs) return false;
+    }
+}
+
+// 2-D tiled TMA load of box (x, y) into shared memory, completing on `bar`.
+__device__ inline void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                   int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ inline void tma_prefetch_desc(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
+
+// record a device-side failure in the plan (first writer wins)
+__device__ inline void raise_status(DevPlan *plan, int code) {
+    atomicCAS(&plan->status, 0, code);
+}
+
+}  // namespace tdg

@@ -1,0 +1,99 @@
+// Host-side declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tdg_common.cuh"
+
+namespace tdg {
+
+enum GemmForm { G_PLAIN = 0, G_SYM = 1, G_ASYM = 2 };
+
+// One operand of a pack kernel: op(X)[x][k] = src[x * sx + k * sk], x < X,
+// k < K, with per-block companders c[(x / L) * cx + (k / L) * cl] (nullptr:
+// plain copy).
+template <typename T>
+struct PackOperand {
+    const T *src;
+    long long sx, sk, X, K;
+    const T *c;
+    long long cx, cl;
+    int L;
+};
+
+template <typename T>
+cudaError_t launch_block_stats(const T *X, long long rows_s, long long cols_s, long long ld,
+                               int L, int trans, int nbc_op, double *mx, double *ss,
+                               DevPlan *plan, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double *eA,
+                           const double *mB, const double *eB, const double *stab,
+                           DevPlan *plan, T *cA, double *sA, T *cB, double *sB, T *pair,
+                           cudaStream_t st);
+
+// Pack kernels run only when the device plan's W equals expectW; W is the
+// packing of the kernel itself; wsign < 0 packs with z, > 0 with z^-1.
+template <typename T>
+cudaError_t launch_pack_k(const PackOperand<T> &o, int W, const DevPlan *plan, int expectW,
+                          int wsign, T *out, long long ldo, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_pack_x(const PackOperand<T> &o, int W, const DevPlan *plan, int expectW,
+                          int wsign, T *out, long long ldo, cudaStream_t st);
+
+cudaError_t launch_codes(const PackOperand<float> &o, int fp8, void *out, long long ldo,
+                         cudaStream_t st);
+
+// Arguments of the CUDA-core packed GEMM (steps c and d).
+template <typename T>
+struct GemmArgs {
+    const DevPlan *plan;
+    long long M, N, K;      // op sizes
+    long long Mrows;        // rows of the A operand's x extent: M, or nM*P (asym)
+    long long Krows;        // rows (k) of both operands: nK*P (sym), K (asym, plain)
+    int L, P;               // block size, packed numbers per block
+    int nM, nK, nN;
+    const T *pair;          // [l][i][j] de-companding factors
+    T *C;
+    long long ldc;
+    T alpha, beta;
+    int beta_zero;
+    T *Rbar;                // nullable: keep packed slab results
+};
+
+// Returns cudaErrorNotSupported when no kernel exists for (T, form, W).
+template <typename T>
+cudaError_t launch_packed_gemm(int form, int W, const GemmArgs<T> &g, const CUtensorMap &mapA,
+                               const CUtensorMap &mapB, cudaStream_t st);
+
+// Tile shape the packed GEMM uses for (T, form): operand boxes are
+// {box_x_a, bk} for A and {box_x_b, bk} for B.
+void packed_gemm_boxes(int dtype, int form, int *box_x_a, int *box_x_b, int *bk);
+
+template <typename T>
+cudaError_t launch_unpack(int form, int W, const GemmArgs<T> &g, int64_t *rint_out,
+                          cudaStream_t st);
+
+cudaError_t launch_snr(const void *C, long long ldc, int dtype, const double *ref, long long ldr,
+                       long long M, long long N, double *out3, cudaStream_t st);
+
+// Tensor-core forms (tcgen05): C = sum_l (s_A s_B) * (A~_l B~_l^T) with both
+// code operands k-major: A~ [M][K], B~ [N][K] (fp16 integers or e4m3).
+struct TcArgs {
+    const DevPlan *plan;
+    long long M, N, K;
+    int L, nM, nK, nN;
+    const float *pair;
+    float *C;
+    long long ldc;
+    float alpha, beta;
+    int beta_zero;
+};
+cudaError_t launch_tc_gemm(int fp8, const TcArgs &a, const CUtensorMap &mapA,
+                           const CUtensorMap &mapB, cudaStream_t st);
+void tc_gemm_boxes(int fp8, int *box_rows_a, int *box_rows_b, int *box_k);
+
+}  // namespace tdg

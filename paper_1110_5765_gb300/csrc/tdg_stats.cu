@@ -1,0 +1,133 @@
+// Step (a), first half: per-block statistics of op(A) and op(B).
+//
+// Sec. 3 gathers max/min of every L x L subblock during the block-major
+// reorder; Sec. 5.B adds sigma.  Here one CTA reads one L x L tile of the
+// stored matrix with 16-byte vector loads (one HBM pass) and produces
+//   max|x|   exact,
+//   sum x^2  fp64 (fp32 inputs: per-thread double-float accumulation of exact
+//            squares, then an fp64 tree), which the planner divides by the
+//            number of valid elements to get sigma^2 about zero.
+// Non-finite inputs raise TDG_ENONFINITE in the plan's device status.
+#include "tdg_common.cuh"
+#include "tdg_internal.h"
+
+namespace tdg {
+
+namespace {
+
+// max|x| is kept as the largest bit pattern of |x| (for non-negative IEEE
+// values the integer order is the numeric order), which stays on the integer
+// pipe; NaN/Inf are flagged separately.
+struct Acc {
+    float hi, lo;              // fp32 path: double-float sum of squares
+    double d;                  // fp64 path
+    unsigned long long mbits;  // bit pattern of the largest |x|
+    int bad;
+};
+
+__device__ inline void add_sq(Acc &a, float x) {
+    // exact square as hi + err (TwoProduct), then TwoSum into (hi, lo)
+    float p = __fmul_rn(x, x);
+    float e = __fmaf_rn(x, x, -p);
+    float t = __fadd_rn(a.hi, p);
+    float bp = __fsub_rn(t, a.hi);
+    float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    a.hi = t;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(err, e));
+    unsigned int b = __float_as_uint(x) & 0x7fffffffu;
+    a.mbits = max(a.mbits, (unsigned long long)b);
+    a.bad |= (b >= 0x7f800000u);
+}
+
+__device__ inline void add_sq(Acc &a, double x) {
+    a.d = __fma_rn(x, x, a.d);
+    unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    a.mbits = max(a.mbits, b);
+    a.bad |= (b >= 0x7ff0000000000000ull);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) block_stats_kernel(const T *__restrict__ X,
+                                                          long long rows_s, long long cols_s,
+                                                          long long ld, int L, int trans,
+                                                          int nbc_op, double *__restrict__ mx,
+                                                          double *__restrict__ ss,
+                                                          DevPlan *plan) {
+    constexpr int VEC = 16 / sizeof(T);
+    const int bj = blockIdx.x, bi = blockIdx.y;
+    const long long r0 = (long long)bi * L, c0 = (long long)bj * L;
+    const int rn = (int)min((long long)L, rows_s - r0);
+    const int cn = (int)min((long long)L, cols_s - c0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const bool vec_ok = (ld % VEC == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+
+    Acc a{0.f, 0.f, 0.0, 0ull, 0};
+    for (int r = warp; r < rn; r += nwarp) {
+        const T *row = X + (r0 + r) * ld + c0;
+        for (int c = lane * VEC; c < cn; c += 32 * VEC) {
+            if (vec_ok && c + VEC <= cn) {
+                if constexpr (sizeof(T) == 4) {
+                    float4 v = __ldg(reinterpret_cast<const float4 *>(row + c));
+                    add_sq(a, v.x); add_sq(a, v.y); add_sq(a, v.z); add_sq(a, v.w);
+                } else {
+                    double2 v = __ldg(reinterpret_cast<const double2 *>(row + c));
+                    add_sq(a, v.x); add_sq(a, v.y);
+                }
+            } else {
+                for (int e = 0; e < VEC && c + e < cn; ++e) add_sq(a, row[c + e]);
+            }
+        }
+    }
+    double s = (sizeof(T) == 4) ? (double)a.hi + (double)a.lo : a.d;
+    double m = (sizeof(T) == 4) ? (double)__uint_as_float((unsigned int)a.mbits)
+                                : __longlong_as_double((long long)a.mbits);
+    int bad = a.bad;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    __shared__ double sh_s[32], sh_m[32];
+    __shared__ int sh_b[32];
+    if (lane == 0) { sh_s[warp] = s; sh_m[warp] = m; sh_b[warp] = bad; }
+    __syncthreads();
+    if (warp == 0) {
+        s = lane < nwarp ? sh_s[lane] : 0.0;
+        m = lane < nwarp ? sh_m[lane] : 0.0;
+        bad = lane < nwarp ? sh_b[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        }
+        if (lane == 0) {
+            long long idx = trans ? (long long)bj * nbc_op + bi : (long long)bi * nbc_op + bj;
+            mx[idx] = m;
+            ss[idx] = s;
+            if (bad) atomicExch(&plan->nonfinite, 1);
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_block_stats(const T *X, long long rows_s, long long cols_s, long long ld,
+                               int L, int trans, int nbc_op, double *mx, double *ss,
+                               DevPlan *plan, cudaStream_t st) {
+    dim3 grid(cdiv_i(cols_s, L), cdiv_i(rows_s, L));
+    block_stats_kernel<T><<<grid, 256, 0, st>>>(X, rows_s, cols_s, ld, L, trans, nbc_op, mx, ss,
+                                                plan);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_block_stats<float>(const float *, long long, long long, long long,
+                                               int, int, int, double *, double *, DevPlan *,
+                                               cudaStream_t);
+template cudaError_t launch_block_stats<double>(const double *, long long, long long,
+                                                long long, int, int, int, double *, double *,
+                                                DevPlan *, cudaStream_t);
+
+}  // namespace tdg
