@@ -1,0 +1,435 @@
+"""Benchmark of the companded-and-packed GEMM on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-forms]
+
+One step is one pass of the whole path — block statistics, device planner,
+companding + packing of A and B, packed GEMM with fused unpack/de-companding —
+on the distortion-sweep workload: M = N = K = 4096, fp32 inputs iid
+uniform[-1, 1], block L = 128, symmetric packing W = 2, distortion target
+20 dB.  Inputs are resident in HBM when timing starts; L2 is flushed between
+steps (a 256 MB write outside the per-step events).  ``value`` is effective
+GFLOP/s = 2 M N K per step over the device time of the steps, summed over all
+ranks (each rank runs its own independent product: weak scaling).
+
+The JSON line also carries:
+  e2e          the same metric through tdgemm_run_host (host buffers, the
+               host-to-device and device-to-host copies inside the timing)
+  roofline     the packed GEMM kernel against the FP32 FMA peak
+  cpu_baseline the CPU oracle on a bounded sample (rank 0, N = 1 only)
+  forms        every other form at the same size with its measured SNR
+  clocks       SM clocks sampled by nvidia-smi during the timed steps
+``--impl reference`` times the CPU oracle itself on host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "effective GFLOP/s (2MNK/t) vs output SNR dB, packed & TC forms vs plain FP64/FP32 GEMM"
+N_SIZE = 4096
+L_BLOCK = 128
+W_PACK = 2
+TARGET_DB = 20.0
+SEED_A, SEED_B = 1112, 1113
+WORKLOAD = ("distortion sweep point: C = A B, M = N = K = 4096, fp32 inputs iid uniform[-1,1], "
+            "block L = 128, per-block adaptive companding, symmetric packing W = 2, "
+            "target 20 dB")
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (one process per GPU, weak scaling)
+# ---------------------------------------------------------------------------
+def dist_setup(ngpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != ngpus:
+        raise SystemExit(f"--gpus {ngpus} but WORLD_SIZE={world}")
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_sample(A, B, budget_s: float = 20.0) -> dict:
+    """The oracle as it stands on one 128 x 128 output tile of the full product:
+    whole-matrix statistics, planning, companding and packing, then the tile
+    over the full K.  Repeated on further tiles while within the budget."""
+    from oracle import oracle as orc
+    st = orc.load_s_table()
+    tiles = synth.sample_tiles(N_SIZE // L_BLOCK, N_SIZE // L_BLOCK, 8, seed=99)
+    t0 = time.perf_counter()
+    done = 0
+    for (ti, tj) in tiles:
+        orc.tdgemm(A, B, L=L_BLOCK, W=W_PACK, dtype="f32", form="sym", target_db=TARGET_DB,
+                   s_table=st, rows=(ti * L_BLOCK, (ti + 1) * L_BLOCK),
+                   cols=(tj * L_BLOCK, (tj + 1) * L_BLOCK))
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = time.perf_counter() - t0
+    flops = 2.0 * L_BLOCK * L_BLOCK * N_SIZE * done
+    return {"value": flops / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": (f"{done} output tile(s) of 128 x 128 over the full K = 4096, each call "
+                       "including statistics, planning, companding and packing of the full "
+                       "4096 x 4096 A and B (single-threaded C + NumPy)"),
+            "seconds": t}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    A = synth.uniform((N_SIZE, N_SIZE), SEED_A, np.float32)
+    B = synth.uniform((N_SIZE, N_SIZE), SEED_B, np.float32)
+    from oracle import oracle as orc
+    orc.build()
+    per_step_budget = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(A, B, budget_s=0.0)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = oracle_sample(A, B, budget_s=per_step_budget)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def launches_per_step(plan) -> int:
+    """Kernels this library queues per tdgemm_run for a target-mode symmetric
+    fp32 plan with fallback, inputs 'N'/'N': block stats x2, planner + scales
+    + de-companding factors, pack A and B for W = 2, plain copy of A for the
+    W = 1 fallback (B is used in place), packed GEMM for W = 2 and plain GEMM
+    for the fallback (kernels not chosen by the planner exit at entry)."""
+    return 2 + 3 + 2 + 1 + 2
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_1110_5765_gb300 import build as b
+    if rank == 0:
+        b.build()
+    barrier(world)
+    import paper_1110_5765_gb300 as tdg
+
+    M = N = K = N_SIZE
+    A_h = synth.uniform((M, K), SEED_A + 17 * rank, np.float32)
+    B_h = synth.uniform((K, N), SEED_B + 17 * rank, np.float32)
+    A = torch.from_numpy(A_h).cuda()
+    B = torch.from_numpy(B_h).cuda()
+    C = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    plan = tdg.Plan(M, N, K, L=L_BLOCK, W=W_PACK, dtype="f32", form="sym",
+                    target_snr_db=TARGET_DB)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.run(A, B, C)
+    torch.cuda.synchronize()
+    info = plan.info()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        plan.quantize_pack(A, B)
+        e1.record(stream)
+        plan.gemm(C)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    gemm_ms = [b_.elapsed_time(c) for _, b_, c in ev]
+    t_steps = sum(step_ms) / 1e3
+    t_max = max_over_ranks(t_steps, world)
+    flops_step = 2.0 * M * N * K
+    value = world * args.steps * flops_step / t_max / 1e9
+
+    # ---- SNR of the timed configuration against the fp64 product
+    ref = torch.matmul(A.double(), B.double())
+    snr = tdg.snr_db(C, ref)
+    del ref
+
+    # ---- roofline of the packed GEMM kernel (FP32 FMA pipe)
+    pk, src = peaks()
+    P = -(-L_BLOCK // W_PACK)
+    Kp = (K // L_BLOCK) * P
+    gemm_flops = 2.0 * M * N * Kp                        # algorithmic: 2 M N K / W
+    gemm_s = statistics.mean(gemm_ms) / 1e3
+    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
+    achieved = gemm_flops / gemm_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "packed_gemm_kernel<float, SYM, W=2> (FP32 FMA pipe)",
+                "peak_source": (f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz "
+                                "(unit counts and maximum SM clock)"),
+                "work_per_launch": "2 M N K / W flops = 6.87e10"}
+
+    # ---- end to end through the host-buffer entry point
+    A_pin = torch.from_numpy(A_h).pin_memory()
+    B_pin = torch.from_numpy(B_h).pin_memory()
+    C_pin = torch.empty((M, N), dtype=torch.float32).pin_memory()
+    plan.run_host(A_pin, B_pin, C_pin)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(e2e_steps):
+        plan.run_host(A_pin, B_pin, C_pin)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    e2e_t = max_over_ranks(s0.elapsed_time(s1) / 1e3, world)
+    e2e = {"value": world * e2e_steps * flops_step / e2e_t / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": A_h.nbytes + B_h.nbytes, "d2h_bytes_per_step": C_pin.numel() * 4,
+           "steps": e2e_steps}
+
+    forms = {}
+    if args.forms and rank == 0:
+        forms = measure_forms(tdg, torch, A, B)
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        cpu = oracle_sample(A_h, B_h, budget_s=20.0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded PCG64 uniform[-1,1])",
+                "config": {"workload": WORKLOAD, "M": M, "N": N, "K": K, "L": L_BLOCK,
+                           "W": W_PACK, "form": "sym", "target_snr_db": TARGET_DB,
+                           "l2": "flushed between steps (256 MB write outside step events)",
+                           "W_used": info["W_used"], "q": info["q"],
+                           "gamma_a": info["gamma_a"], "gamma_b": info["gamma_b"],
+                           "pred_snr_db": info["pred_snr_db"], "snr_db": snr,
+                           "parallelism": f"replicas x{world}"},
+                "gpu_launches": launches_per_step(plan) * args.steps,
+                "wall_s": wall,
+                "gemm_ms": statistics.mean(gemm_ms),
+                "pack_ms": statistics.mean([a.elapsed_time(b_) for a, b_, _ in ev]),
+                "roofline": roofline, "e2e": e2e, "clocks": clocks,
+                "peaks_source": src}
+        if cpu is not None:
+            line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        if forms:
+            line["forms"] = forms
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _time(fn, torch, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(reps):
+        fn()
+    s1.record()
+    torch.cuda.synchronize()
+    return s0.elapsed_time(s1) / 1e3 / reps
+
+
+def measure_forms(tdg, torch, A32, B32) -> dict:
+    """Every form at 4096^3 beside plain fp32/fp64 GEMM on the same GPU:
+    effective GFLOP/s (whole path) and SNR against the fp64 product."""
+    n = N_SIZE
+    flops = 2.0 * n ** 3
+    out = {}
+    ref = torch.matmul(A32.double(), B32.double())
+    A64, B64 = A32.double(), B32.double()
+    torch.backends.cuda.matmul.allow_tf32 = False
+    C32 = torch.empty_like(A32)
+    C64 = torch.empty_like(A64)
+
+    def rec(name, t, C, extra=None):
+        d = {"gflops": flops / t / 1e9, "ms": t * 1e3, "snr_db": tdg.snr_db(C, ref)}
+        if extra:
+            d.update(extra)
+        out[name] = d
+
+    rec("cublas_f32", _time(lambda: torch.matmul(A32, B32, out=C32), torch), C32)
+    rec("cublas_f64", _time(lambda: torch.matmul(A64, B64, out=C64), torch, reps=1), C64)
+    cases = [
+        ("plain_f32", dict(dtype="f32", form="plain", W=1, bits=0), A32, B32),
+        ("plain_f64", dict(dtype="f64", form="plain", W=1, bits=0), A64, B64),
+        ("sym_f32_W2_20dB", dict(dtype="f32", form="sym", W=2, target_snr_db=20.0), A32, B32),
+        ("asym_f32_W2_20dB", dict(dtype="f32", form="asym", W=2, target_snr_db=20.0), A32, B32),
+        ("sym_f32_W2_40dB", dict(dtype="f32", form="sym", W=2, target_snr_db=40.0), A32, B32),
+        ("sym_f64_W2_40dB", dict(dtype="f64", form="sym", W=2, target_snr_db=40.0), A64, B64),
+        ("sym_f64_W3_40dB", dict(dtype="f64", form="sym", W=3, target_snr_db=40.0), A64, B64),
+        ("asym_f64_W3_40dB", dict(dtype="f64", form="asym", W=3, target_snr_db=40.0), A64, B64),
+        ("sym_f64_W4_20dB", dict(dtype="f64", form="sym", W=4, target_snr_db=20.0), A64, B64),
+        ("tc_int_8bit", dict(dtype="f32", form="tc_int", W=1, bits=8), A32, B32),
+        ("tc_int_40dB", dict(dtype="f32", form="tc_int", W=1, target_snr_db=40.0), A32, B32),
+        ("tc_fp8", dict(dtype="f32", form="tc_fp8", W=1, bits=0), A32, B32),
+    ]
+    for name, kw, A, B in cases:
+        try:
+            p = tdg.Plan(n, n, n, L=L_BLOCK, **kw)
+            C = C64 if kw["dtype"] == "f64" and not kw["form"].startswith("tc") else C32
+            reps = 1 if kw["dtype"] == "f64" else 3
+            t = _time(lambda: p.run(A, B, C), torch, reps=reps)
+            info = p.info()
+            rec(name, t, C, {"W_used": info["W_used"], "pred_snr_db": info["pred_snr_db"]})
+            p.close()
+        except Exception as e:     # a form not built yet is reported, not hidden
+            out[name] = {"error": str(e)[:200]}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tdgemm", choices=["tdgemm", "reference"])
+    ap.add_argument("--no-forms", dest="forms", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -47,10 +47,10 @@ def level_range(L: int, dtype: str):
     return range(t, orc.T_MAX[dtype] + 1)
 
 
-def calibrate_one(dtype: str, form: str, W: int, L: int) -> dict:
+def calibrate_one(dtype: str, form: str, W: int, L: int, ts=None) -> dict:
     T = orc.NP_T[dtype]
     out = {}
-    for t in level_range(L, dtype):
+    for t in (ts if ts is not None else level_range(L, dtype)):
         R = orc.r_level(t)
         q = orc.q_for(R)
         gA = min(GAMMA_A_CAL, R // L)

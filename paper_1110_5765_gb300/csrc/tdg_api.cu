@@ -380,20 +380,20 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
                                      ((uintptr_t)B & 15) == 0;
                 if (!directA)
                     CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, nullptr), 1, p->dplan, 1, 0,
-                                            (T *)p->Abuf, s.a_ld, st));
+                                            (T *)p->Abuf, s.a_ld, s.a_rows, st));
                 if (!directB)
                     CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, nullptr), 1, p->dplan, 1, 0,
-                                            (T *)p->Bbuf, s.b_ld, st));
+                                            (T *)p->Bbuf, s.b_ld, s.b_rows, st));
             } else if (p->form == TDG_SYM) {
                 CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w, -1,
-                                        (T *)p->Abuf, s.a_ld, st));                   // eq. 6
+                                        (T *)p->Abuf, s.a_ld, s.a_rows, st));                   // eq. 6
                 CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, (const T *)p->cB), w, p->dplan, w, +1,
-                                        (T *)p->Bbuf, s.b_ld, st));                   // eq. 7
+                                        (T *)p->Bbuf, s.b_ld, s.b_rows, st));                   // eq. 7
             } else {
                 CU_TRY(launch_pack_x<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w, -1,
                                         (T *)p->Abuf, s.a_ld, st));                   // eq. 11
                 CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, (const T *)p->cB), 1, p->dplan, w, 0,
-                                        (T *)p->Bbuf, s.b_ld, st));                   // b~ only
+                                        (T *)p->Bbuf, s.b_ld, s.b_rows, st));                   // b~ only
             }
         }
     }

@@ -147,14 +147,19 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         Q = pow2_t(T(0), g.plan->q);
     }
 
-    // block indices of this thread's fragment groups (clamped inside the grid)
-    int iblk[RG], jblk[CG];
+    // row-block index of every fragment row (clamped inside the grid): rows
+    // are m (a 4-row group never straddles a block since L % 16 == 0) or, for
+    // the asymmetric form, packed rows with P = ceil(L / W) per block, which
+    // can straddle when P % 4 != 0 (W = 3)
+    int iblk[TM], jblk[CG];
 #pragma unroll
-    for (int gi = 0; gi < RG; ++gi) {
-        long long xr = x0 + gi * (BM / RG) + ty * 4;
-        long long ib = FORM == G_ASYM ? xr / g.P : xr / g.L;
-        iblk[gi] = (int)min(ib, (long long)g.nM - 1);
-    }
+    for (int gi = 0; gi < RG; ++gi)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            long long xr = x0 + gi * (BM / RG) + ty * 4 + e;
+            long long ib = FORM == G_ASYM ? xr / g.P : xr / g.L;
+            iblk[gi * 4 + e] = (int)min(ib, (long long)g.nM - 1);
+        }
 #pragma unroll
     for (int hj = 0; hj < CG; ++hj) {
         long long nc = n0 + hj * (BN / CG) + tx * 4;
@@ -215,11 +220,11 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
 #pragma unroll
             for (int gi = 0; gi < RG; ++gi)
 #pragma unroll
-                for (int hj = 0; hj < CG; ++hj) {
-                    const T pr =
-                        g.pair[((long long)l * g.nM + iblk[gi]) * g.nN + jblk[hj]];
+                for (int hj = 0; hj < CG; ++hj)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
+                    for (int e = 0; e < 4; ++e) {
+                        const T pr = g.pair[((long long)l * g.nM + iblk[gi * 4 + e]) * g.nN +
+                                            jblk[hj]];
 #pragma unroll
                         for (int f = 0; f < 4; ++f) {
                             const int i = gi * 4 + e, j = hj * 4 + f;

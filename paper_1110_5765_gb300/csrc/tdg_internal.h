@@ -35,10 +35,11 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
                            cudaStream_t st);
 
 // Pack kernels run only when the device plan's W equals expectW; W is the
-// packing of the kernel itself; wsign < 0 packs with z, > 0 with z^-1.
+// packing of the kernel itself; wsign < 0 packs with z, > 0 with z^-1;
+// rows_out bounds the rows written to the k-major output.
 template <typename T>
 cudaError_t launch_pack_k(const PackOperand<T> &o, int W, const DevPlan *plan, int expectW,
-                          int wsign, T *out, long long ldo, cudaStream_t st);
+                          int wsign, T *out, long long ldo, long long rows_out, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_pack_x(const PackOperand<T> &o, int W, const DevPlan *plan, int expectW,

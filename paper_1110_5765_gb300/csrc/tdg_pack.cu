@@ -88,7 +88,7 @@ __device__ inline void stage_tile(const Src<T> &S, T *s, int pitch, long long x0
 template <typename T, int W>
 __global__ void __launch_bounds__(256) pack_k_kernel(Src<T> S, int P, const DevPlan *plan,
                                                      int expectW, int wsign, T *out,
-                                                     long long ldo) {
+                                                     long long ldo, long long rows_out) {
     if (plan->W != expectW) return;   // the device planner chose another packing
     const T w = W > 1 ? pack_weight<T>(plan, wsign) : T(1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) pack_k_kernel(Src<T> S, int P, const DevP
         int jr = e / TILE, xr = e % TILE;
         int j = j0 + jr;
         long long x = x0 + xr;
-        if (j >= P || x >= S.X) continue;
+        if (j >= P || x >= S.X || l * P + j >= rows_out) continue;
         const T *d = s + xr * pitch + jr * W;
         T acc = d[W - 1];
 #pragma unroll
@@ -200,13 +200,13 @@ Src<T> make_src(const PackOperand<T> &o) {
 
 template <typename T, int W>
 cudaError_t launch_pack_k_w(const PackOperand<T> &o, const DevPlan *plan, int expectW, int wsign,
-                            T *out, long long ldo, cudaStream_t st) {
+                            T *out, long long ldo, long long rows_out, cudaStream_t st) {
     Src<T> S = make_src(o);
     int P = (o.L + W - 1) / W;
     int nK = cdiv_i(o.K, o.L);
     dim3 grid(cdiv_i(o.X, TILE), nK * cdiv_i(P, TILE));
     size_t sm = (size_t)TILE * (TILE * W + 1) * sizeof(T);
-    pack_k_kernel<T, W><<<grid, 256, sm, st>>>(S, P, plan, expectW, wsign, out, ldo);
+    pack_k_kernel<T, W><<<grid, 256, sm, st>>>(S, P, plan, expectW, wsign, out, ldo, rows_out);
     return cudaGetLastError();
 }
 
@@ -226,12 +226,12 @@ cudaError_t launch_pack_x_w(const PackOperand<T> &o, const DevPlan *plan, int ex
 
 template <typename T>
 cudaError_t launch_pack_k(const PackOperand<T> &o, int W, const DevPlan *plan, int expectW,
-                          int wsign, T *out, long long ldo, cudaStream_t st) {
+                          int wsign, T *out, long long ldo, long long rows_out, cudaStream_t st) {
     switch (W) {
-        case 1: return launch_pack_k_w<T, 1>(o, plan, expectW, wsign, out, ldo, st);
-        case 2: return launch_pack_k_w<T, 2>(o, plan, expectW, wsign, out, ldo, st);
-        case 3: return launch_pack_k_w<T, 3>(o, plan, expectW, wsign, out, ldo, st);
-        case 4: return launch_pack_k_w<T, 4>(o, plan, expectW, wsign, out, ldo, st);
+        case 1: return launch_pack_k_w<T, 1>(o, plan, expectW, wsign, out, ldo, rows_out, st);
+        case 2: return launch_pack_k_w<T, 2>(o, plan, expectW, wsign, out, ldo, rows_out, st);
+        case 3: return launch_pack_k_w<T, 3>(o, plan, expectW, wsign, out, ldo, rows_out, st);
+        case 4: return launch_pack_k_w<T, 4>(o, plan, expectW, wsign, out, ldo, rows_out, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -258,9 +258,9 @@ cudaError_t launch_codes(const PackOperand<float> &o, int fp8, void *out, long l
 }
 
 template cudaError_t launch_pack_k<float>(const PackOperand<float> &, int, const DevPlan *, int, int,
-                                          float *, long long, cudaStream_t);
+                                          float *, long long, long long, cudaStream_t);
 template cudaError_t launch_pack_k<double>(const PackOperand<double> &, int, const DevPlan *, int, int,
-                                          double *, long long, cudaStream_t);
+                                          double *, long long, long long, cudaStream_t);
 template cudaError_t launch_pack_x<float>(const PackOperand<float> &, int, const DevPlan *, int, int,
                                           float *, long long, cudaStream_t);
 template cudaError_t launch_pack_x<double>(const PackOperand<double> &, int, const DevPlan *, int, int,

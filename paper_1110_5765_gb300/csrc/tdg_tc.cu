@@ -1,17 +1,313 @@
-// Tensor-core form (placeholder until the tcgen05 kernel lands).
+// Tensor-core form of step (c): the companded blocks multiplied on the 5th
+// generation tensor cores (tcgen05), the per-slab "promotion" of (d) in
+// registers.
+//
+//   TDG_TC_INT  a~, b~ are the integers of eq. 3 (|a~| <= gamma <= 2047) held
+//               exactly in fp16; kind::f16 products are exact and every
+//               partial sum of one slab stays below 2^24, so the fp32
+//               accumulator in tensor memory holds eq. 4's integer exactly.
+//   TDG_TC_FP8  a~, b~ are E4M3 codes (kind::f8f6f4), fp32 accumulation.
+//
+// C = sum_l (s_A,il s_B,lj) * (A~_l B~_l^T), slabs l of L k-values.
+//
+// CTA tile 128 x 256, one CTA per SM (192 KB of shared memory):
+//   warp 0      allocates 512 TMEM columns; lane 0 streams 128-byte-wide k
+//               boxes of A~ (128 rows) and B~ (256 rows) with 2-D TMA
+//               (128-byte swizzle, no multicast) into a 4-deep ring;
+//   warp 1      lane 0 issues tcgen05.mma (M = 128, N = 256) into one of two
+//               TMEM accumulators, a fresh accumulation per slab, and
+//               commits to mbarriers that free ring stages and hand a full
+//               slab to the epilogue;
+//   warps 2..17 epilogue: each thread owns one output row and 64 columns;
+//               per slab it reads its TMEM lane (tcgen05.ld), applies
+//               C_acc = fma(r, s_A s_B, C_acc) in fp32 and releases the
+//               accumulator, so the next-but-one slab's MMAs can reuse it
+//               while this one is being promoted.
+// Every wait is bounded (2 s of global time); on expiry the CTA records
+// TDG_ETIMEOUT, drains what it issued (bounded) and frees its TMEM.
+#include <cuda_fp16.h>
+
 #include "tdg_common.cuh"
 #include "tdg_internal.h"
 
 namespace tdg {
 
-cudaError_t launch_tc_gemm(int, const TcArgs &, const CUtensorMap &, const CUtensorMap &,
-                           cudaStream_t) {
-    return cudaErrorNotSupported;
+namespace {
+
+constexpr int BM = 128, BN = 256;
+constexpr int STAGES = 4;
+constexpr int ROW_BYTES = 128;                       // k-bytes per stage (one swizzle row)
+constexpr int STAGE_A = BM * ROW_BYTES;              // 16 KB
+constexpr int STAGE_B = BN * ROW_BYTES;              // 32 KB
+constexpr int EPI_COLS = 64;                         // output columns per epilogue thread
+constexpr int EPI_WARPS = 4 * (BN / EPI_COLS);       // 4 TMEM lane quadrants x column groups
+constexpr int NUM_THREADS = 32 * (2 + EPI_WARPS);
+constexpr int TMEM_COLS = 512;                       // 2 accumulators x 256 fp32 columns
+constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * (STAGE_A + STAGE_B) + 256;
+
+// UMMA shared-memory descriptor, K-major operand with 128-byte swizzle:
+// 8-row x 128-byte atoms, 1024 bytes between 8-row groups.
+__device__ inline uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);      // start address
+    d |= (uint64_t)(16 >> 4) << 16;               // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset
+    d |= (uint64_t)1 << 46;                       // descriptor version
+    d |= (uint64_t)2 << 61;                       // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: D fp32, A/B fp16 (or E4M3 under kind::f8f6f4,
+// whose format code is also 0), both K-major, N = 256, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+template <int FP8>
+__device__ inline void mma(uint32_t dtmem, uint64_t ad, uint64_t bd, int accumulate) {
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate));
+    }
+}
+
+__device__ inline void mma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ inline void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ inline void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 lanes x 32 bits, 16 consecutive columns per thread
+__device__ inline void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int FP8>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                   const __grid_constant__ CUtensorMap mapB, const TcArgs g) {
+    constexpr int BK = FP8 ? 128 : 64;          // k elements per stage
+    constexpr int KSTEP_BYTES = 32;             // one MMA: 16 fp16 or 32 e4m3 values
+    constexpr int MMAS_PER_STAGE = ROW_BYTES / KSTEP_BYTES;
+
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte alignment for the swizzled operand tiles
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = smem;
+    unsigned char *sB = smem + STAGES * STAGE_A;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + STAGES * STAGE_B);
+    uint64_t *full = bars;                       // [STAGES]  TMA -> MMA
+    uint64_t *empty = bars + STAGES;             // [STAGES]  MMA -> TMA
+    uint64_t *acc_full = bars + 2 * STAGES;      // [2]       MMA -> epilogue
+    uint64_t *acc_empty = bars + 2 * STAGES + 2; // [2]       epilogue -> MMA
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
+    int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long m0 = (long long)blockIdx.y * BM, n0 = (long long)blockIdx.x * BN;
+    const int slab_stages = g.L / BK;
+    const int nslab = g.nK;
+    const int total = nslab * slab_stages;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], EPI_WARPS);
+        }
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            tma_prefetch_desc(&mapA);
+            tma_prefetch_desc(&mapB);
+            int it = 0;
+            for (; it < total; ++it) {
+                const int stage = it % STAGES;
+                if (it >= STAGES && !mbar_wait_bounded(&empty[stage], ((it / STAGES) + 1) & 1)) {
+                    raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);
+                    *abort_flag = 1;
+                    break;
+                }
+                if (*(volatile int *)abort_flag) break;
+                const int l = it / slab_stages, ks = it % slab_stages;
+                const int kx = l * g.L + ks * BK;
+                mbar_arrive_expect_tx(&full[stage], STAGE_A + STAGE_B);
+                tma_load_2d(sA + stage * STAGE_A, &mapA, &full[stage], kx, (int)m0);
+                tma_load_2d(sB + stage * STAGE_B, &mapB, &full[stage], kx, (int)n0);
+            }
+            // every copy issued must land before the CTA can exit
+            for (int k = max(0, it - STAGES); k < it; ++k)
+                mbar_wait_bounded(&full[k % STAGES], (k / STAGES) & 1);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int l = 0; l < nslab && ok; ++l) {
+                const int b = l & 1;
+                if (l >= 2 && !mbar_wait_bounded(&acc_empty[b], ((l >> 1) + 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                for (int ks = 0; ks < slab_stages; ++ks, ++it) {
+                    const int stage = it % STAGES;
+                    if (!mbar_wait_bounded(&full[stage], (it / STAGES) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = desc_sw128(smem_u32(sA + stage * STAGE_A));
+                    const uint64_t bd = desc_sw128(smem_u32(sB + stage * STAGE_B));
+#pragma unroll
+                    for (int kk = 0; kk < MMAS_PER_STAGE; ++kk) {
+                        const uint64_t adv = (uint64_t)((kk * KSTEP_BYTES) >> 4);
+                        mma<FP8>(d, ad + adv, bd + adv, (ks | kk) != 0);
+                    }
+                    mma_commit(&empty[stage]);          // frees the stage when done
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[b]);               // slab l is complete in TMEM
+            }
+            if (!ok) {
+                raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);
+                *abort_flag = 1;
+            }
+            // wait for this thread's last MMAs before the TMEM can be freed
+            if (it > 0) mbar_wait_bounded(&empty[(it - 1) % STAGES], ((it - 1) / STAGES) & 1);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int ew = warp - 2;
+        const int quad = warp & 3;                     // TMEM lanes 32*quad .. +31
+        const int cgrp = ew >> 2;                      // columns [EPI_COLS*cgrp, +EPI_COLS)
+        const long long row = m0 + quad * 32 + lane;
+        const int iblk = (int)min(row / g.L, (long long)g.nM - 1);
+        float cacc[EPI_COLS];
+#pragma unroll
+        for (int c = 0; c < EPI_COLS; ++c) cacc[c] = 0.f;
+        bool ok = true;
+        for (int l = 0; l < nslab; ++l) {
+            const int b = l & 1;
+            if (!mbar_wait_bounded(&acc_full[b], (l >> 1) & 1)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t base =
+                tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN + cgrp * EPI_COLS);
+#pragma unroll
+            for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
+                float v[16];
+                tmem_ld16(base + ch * 16, v);
+                const long long col0 = n0 + cgrp * EPI_COLS + ch * 16;
+                const int jblk = (int)min(col0 / g.L, (long long)g.nN - 1);
+                const float pr = g.pair[((long long)l * g.nM + iblk) * g.nN + jblk];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) cacc[ch * 16 + e] = __fmaf_rn(v[e], pr, cacc[ch * 16 + e]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+        if (!ok) {
+            raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);
+            *abort_flag = 1;
+        } else if (row < g.M) {
+            float *crow = g.C + row * g.ldc;
+#pragma unroll
+            for (int c = 0; c < EPI_COLS; ++c) {
+                const long long col = n0 + cgrp * EPI_COLS + c;
+                if (col < g.N)
+                    crow[col] = g.beta_zero ? __fmul_rn(g.alpha, cacc[c])
+                                            : __fmaf_rn(g.alpha, cacc[c], __fmul_rn(g.beta, crow[col]));
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_tc_gemm(int fp8, const TcArgs &a, const CUtensorMap &mapA,
+                           const CUtensorMap &mapB, cudaStream_t st) {
+    dim3 grid((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM));
+    if (fp8) {
+        static bool set = false;
+        if (!set) {
+            cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<1>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)SMEM_BYTES);
+            if (e != cudaSuccess) return e;
+            set = true;
+        }
+        tc_gemm_kernel<1><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(mapA, mapB, a);
+    } else {
+        static bool set = false;
+        if (!set) {
+            cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<0>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)SMEM_BYTES);
+            if (e != cudaSuccess) return e;
+            set = true;
+        }
+        tc_gemm_kernel<0><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(mapA, mapB, a);
+    }
+    return cudaGetLastError();
 }
 
 void tc_gemm_boxes(int fp8, int *box_rows_a, int *box_rows_b, int *box_k) {
-    *box_rows_a = 128;
-    *box_rows_b = 128;
+    *box_rows_a = BM;
+    *box_rows_b = BN;
     *box_k = fp8 ? 128 : 64;
 }
 

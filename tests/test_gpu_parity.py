@@ -265,3 +265,17 @@ def test_distortion_sweep_size_sampled_tiles(tdg, orc, form):
         rows, cols = (ti * 128, ti * 128 + 128), (tj * 128, tj * 128 + 128)
         ref = orc.tdgemm(A, B, L=128, W=2, dtype="f32", form=form, bits=6, rows=rows, cols=cols)
         assert same_bits(g["C"][rows[0]:rows[1], cols[0]:cols[1]], ref.C), (ti, tj)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("form", ["sym", "asym"])
+@pytest.mark.parametrize("W", [1, 2, 3, 4])
+def test_fixed_bits_per_block_companders(tdg, orc, dtype, form, W):
+    """Per-block companders that differ block to block (Laplacian rows scaled
+    per block), ragged sizes, every W: bit-identical to the oracle."""
+    T = NP[dtype]
+    A = synth.laplace((200, 300), 91, T) * np.repeat(np.linspace(0.5, 4, 4), 64)[:200, None].astype(T)
+    B = synth.laplace((300, 150), 92, T)
+    ref = orc.tdgemm(A, B, L=64, W=W, dtype=dtype, form=form, bits=6)
+    g = run_gpu(tdg, A, B, L=64, W=W, dtype=dtype, form=form, bits=6)
+    assert same_bits(g["C"], ref.C)
