@@ -96,8 +96,8 @@ def test_tc_fp8_matches_oracle(tdg, orc):
     Bq = np.abs(orc.e4m3((B * cB).astype(np.float64)))
     bound = np.zeros((256, 320))
     for l in range(4):
-        bound += (Aq[:, l * 128:(l + 1) * 128] @ Bq[l * 128:(l + 1) * 128]) * \
-            np.outer(ref.sA[:, l], ref.sB[l, :])
+        scale = np.repeat(np.repeat(np.outer(ref.sA[:, l], ref.sB[l, :]), 128, 0), 128, 1)
+        bound += (Aq[:, l * 128:(l + 1) * 128] @ Bq[l * 128:(l + 1) * 128]) * scale[:256, :320]
     bound = bound * 128 * 2.0**-23 + 4 * 2.0**-24 * np.abs(ref.C)
     assert np.all(np.abs(C.astype(np.float64) - ref.C) <= bound + 1e-30)
     ex = orc.exact_gemm(A, B)
