@@ -81,7 +81,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.out, stderr=subprocess.DEVNULL)
         except FileNotFoundError:
             self.proc = None
@@ -284,18 +284,19 @@ def run_gpu(args):
 
     # ---- roofline of the packed GEMM kernel (FP32 FMA pipe)
     pk, src = peaks()
-    P = -(-L_BLOCK // W_PACK)
-    Kp = (K // L_BLOCK) * P
+    W_used = max(1, info["W_used"])
+    P = -(-L_BLOCK // W_used)
+    Kp = (K // L_BLOCK) * P if W_used > 1 else K
     gemm_flops = 2.0 * M * N * Kp                        # algorithmic: 2 M N K / W
     gemm_s = statistics.mean(gemm_ms) / 1e3
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
     achieved = gemm_flops / gemm_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
-                "kernel": "packed_gemm_kernel<float, SYM, W=2> (FP32 FMA pipe)",
+                "kernel": f"packed_gemm_kernel<float, {'SYM' if W_used > 1 else 'PLAIN'}, W={W_used}> (FP32 FMA pipe)",
                 "peak_source": (f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz "
                                 "(unit counts and maximum SM clock)"),
-                "work_per_launch": "2 M N K / W flops = 6.87e10"}
+                "work_per_launch": f"2 M N K / W flops = {gemm_flops:.3e}"}
 
     # ---- end to end through the host-buffer entry point
     A_pin = torch.from_numpy(A_h).pin_memory()
@@ -414,15 +415,45 @@ def measure_forms(tdg, torch, A32, B32) -> dict:
     return out
 
 
+def profile_case(form: str, n: int):
+    """A small case for ncu captures: three runs of one plan, no timing."""
+    import torch
+    from paper_1110_5765_gb300 import build as b
+    b.build()
+    import paper_1110_5765_gb300 as tdg
+    A = torch.from_numpy(synth.uniform((n, n), 1, np.float32)).cuda()
+    B = torch.from_numpy(synth.uniform((n, n), 2, np.float32)).cuda()
+    if form.startswith("tc"):
+        p = tdg.Plan(n, n, n, L=L_BLOCK, W=1, dtype="f32", form=form,
+                     bits=8 if form == "tc_int" else 0)
+    elif form == "plain":
+        p = tdg.Plan(n, n, n, L=L_BLOCK, W=1, dtype="f32", form="plain")
+    else:
+        p = tdg.Plan(n, n, n, L=L_BLOCK, W=W_PACK, dtype="f32", form=form,
+                     target_snr_db=TARGET_DB)
+    C = torch.empty((n, n), device="cuda")
+    for _ in range(3):
+        p.run(A, B, C)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": form, "n": n, "info": p.info()}))
+    p.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tdgemm", choices=["tdgemm", "reference"])
     ap.add_argument("--no-forms", dest="forms", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--profile-case", default=None,
+                    help="plain|sym|asym|tc_int|tc_fp8: run a small case three times for ncu")
+    ap.add_argument("--size", type=int, default=2048)
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case, args.size)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
