@@ -195,6 +195,31 @@ tdg_status tdgemm_plan_destroy(tdgemm_plan_t plan);
 tdg_status tdgemm_snr(const void *C, int64_t ldc, tdg_dtype dtype, const double *ref,
                       int64_t ldr, int64_t M, int64_t N, double *out3, void *stream);
 
+/*
+ * One-shot fixed-bit product that allocates nothing:
+ *     C = alpha * op(A) * op(B) + beta * C
+ * with the statistics, companders, de-companding factors and packed operands
+ * in one static device array of 32 MiB that the library holds on every GPU
+ * that loads it, instead of plan workspace from cudaMalloc.  For callers that
+ * may not allocate device memory where they call: code running while a stream
+ * is captured into a CUDA graph, allocators that own the whole device, and
+ * latency-bound services that must not allocate on first use.
+ *   form     TDG_SYM or TDG_ASYM; W 1..4; bits 2..20 (gamma = 2^(bits-1) - 1);
+ *            other arguments as in tdgemm_plan / tdgemm_gemm.  A, B, C device.
+ * Results equal those of tdgemm_plan + tdgemm_run with the same arguments.
+ * A product whose workspace exceeds the 32 MiB is rejected with TDG_EINVAL
+ * before any device work.  Every call reuses the same array (it keeps the
+ * previous call's contents; each call clears what must start at zero), so
+ * calls whose device work overlaps — different streams, or threads sharing a
+ * device — race: order them on one stream.  The first call on a device looks
+ * up the array's device address (with that device current); make it before
+ * any stream capture begins.  The paper has no counterpart to this entry point.
+ */
+tdg_status tdgemm_run_static(char transA, char transB, int64_t M, int64_t N, int64_t K,
+                             int64_t lda, int64_t ldb, int64_t ldc, int L, int W,
+                             tdg_dtype dtype, tdg_form form, int bits, const void *A,
+                             const void *B, void *C, double alpha, double beta, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *tdgemm_last_error(void);
 

@@ -23,7 +23,8 @@ STATUS = {0: "TDG_OK", 1: "TDG_EINVAL", 2: "TDG_ENOMEM", 3: "TDG_ECUDA", 4: "TDG
 # every symbol include/tdgemm.h declares
 EXPORTS = ["tdgemm_plan", "tdgemm_set_rep_noise", "tdgemm_set_manual", "tdgemm_quantize_pack",
            "tdgemm_gemm", "tdgemm_run", "tdgemm_run_host", "tdgemm_unpack", "tdgemm_plan_info",
-           "tdgemm_plan_destroy", "tdgemm_snr", "tdgemm_last_error", "tdgemm_version"]
+           "tdgemm_plan_destroy", "tdgemm_snr", "tdgemm_run_static", "tdgemm_last_error",
+           "tdgemm_version"]
 
 
 class Info(ctypes.Structure):
@@ -64,6 +65,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.tdgemm_plan_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.tdgemm_plan_destroy.argtypes = [vp]
     L.tdgemm_snr.argtypes = [vp, i64, i32, vp, i64, i64, i64, vp, vp]
+    L.tdgemm_run_static.argtypes = [ctypes.c_char, ctypes.c_char, i64, i64, i64, i64, i64, i64,
+                                    i32, i32, i32, i32, i32, vp, vp, vp, dbl, dbl, vp]
     L.tdgemm_last_error.restype = ctypes.c_char_p
     L.tdgemm_version.restype = ctypes.c_char_p
     for name in EXPORTS:

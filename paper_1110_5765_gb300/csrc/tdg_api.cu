@@ -29,6 +29,9 @@ static tdg_status fail(tdg_status st, const char *fmt, ...) {
     return st;
 }
 
+// lets other translation units report through tdgemm_last_error()
+void tdg::record_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 #define CU_TRY(expr)                                                                  \
     do {                                                                              \
         cudaError_t e_ = (expr);                                                      \

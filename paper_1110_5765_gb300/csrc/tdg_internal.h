@@ -78,6 +78,9 @@ template <typename T>
 cudaError_t launch_unpack(int form, int W, const GemmArgs<T> &g, int64_t *rint_out,
                           cudaStream_t st);
 
+// store a message for tdgemm_last_error() on this thread
+void record_error(const char *msg);
+
 cudaError_t launch_snr(const void *C, long long ldc, int dtype, const double *ref, long long ldr,
                        long long M, long long N, double *out3, cudaStream_t st);
 
