@@ -143,41 +143,52 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time (the job finishes when the last rank does)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(world: int, steps: int, flops_per_step: float, t_max: float) -> float:
+    """Effective GFLOP/s of the whole job: every rank runs its own product
+    (weak scaling), so the work is world x steps x 2MNK over the slowest rank's
+    time."""
+    return world * steps * flops_per_step / t_max / 1e9
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle leg (bounded sample)
 # ---------------------------------------------------------------------------
-def oracle_sample(A, B, budget_s: float = 20.0) -> dict:
-    """The oracle as it stands on one 128 x 128 output tile of the full product:
-    whole-matrix statistics, planning, companding and packing, then the tile
-    over the full K.  Repeated on further tiles while within the budget."""
+def oracle_sample(A, B, budget_s: float = 20.0, max_tiles: int = 64) -> dict:
+    """The CPU oracle, as it stands, on sampled output tiles of the workload:
+    for one 128 x 128 output tile it runs the whole path (statistics,
+    planning, companding, packing, packed product, unpacking) on the 128-row
+    panel of A and the 128-column panel of B the tile depends on (full K).
+    Tiles are taken until ``budget_s`` seconds have passed (at least one)."""
     from oracle import oracle as orc
     st = orc.load_s_table()
-    tiles = synth.sample_tiles(N_SIZE // L_BLOCK, N_SIZE // L_BLOCK, 8, seed=99)
+    tiles = synth.sample_tiles(N_SIZE // L_BLOCK, N_SIZE // L_BLOCK, max_tiles, seed=99)
     t0 = time.perf_counter()
     done = 0
     for (ti, tj) in tiles:
-        orc.tdgemm(A, B, L=L_BLOCK, W=W_PACK, dtype="f32", form="sym", target_db=TARGET_DB,
-                   s_table=st, rows=(ti * L_BLOCK, (ti + 1) * L_BLOCK),
-                   cols=(tj * L_BLOCK, (tj + 1) * L_BLOCK))
+        Ap = np.ascontiguousarray(A[ti * L_BLOCK:(ti + 1) * L_BLOCK])
+        Bp = np.ascontiguousarray(B[:, tj * L_BLOCK:(tj + 1) * L_BLOCK])
+        orc.tdgemm(Ap, Bp, L=L_BLOCK, W=W_PACK, dtype="f32", form="sym", target_db=TARGET_DB,
+                   s_table=st)
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
     t = time.perf_counter() - t0
     flops = 2.0 * L_BLOCK * L_BLOCK * N_SIZE * done
     return {"value": flops / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": (f"{done} output tile(s) of 128 x 128 over the full K = 4096, each call "
-                       "including statistics, planning, companding and packing of the full "
-                       "4096 x 4096 A and B (single-threaded C + NumPy)"),
+            "sample": (f"{done} output tile(s) of 128 x 128, each the whole companded-and-"
+                       "packed path on its 128 x 4096 panel of A and 4096 x 128 panel of B "
+                       "(single-threaded C + NumPy oracle)"),
             "seconds": t}
 
 
@@ -190,9 +201,10 @@ def run_reference(args):
     B = synth.uniform((N_SIZE, N_SIZE), SEED_B, np.float32)
     from oracle import oracle as orc
     orc.build()
-    per_step_budget = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    # the whole run stays within about three minutes whatever K and W are
+    per_step_budget = max(0.05, 150.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_sample(A, B, budget_s=0.0)
+        oracle_sample(A, B, budget_s=0.0, max_tiles=1)
     vals, secs = [], 0.0
     for _ in range(args.steps):
         r = oracle_sample(A, B, budget_s=per_step_budget)
@@ -275,7 +287,7 @@ def run_gpu(args):
     t_steps = sum(step_ms) / 1e3
     t_max = max_over_ranks(t_steps, world)
     flops_step = 2.0 * M * N * K
-    value = world * args.steps * flops_step / t_max / 1e9
+    value = whole_job_value(world, args.steps, flops_step, t_max)
 
     # ---- SNR of the timed configuration against the fp64 product
     ref = torch.matmul(A.double(), B.double())
@@ -439,6 +451,46 @@ def profile_case(form: str, n: int):
     p.close()
 
 
+def sweep(out_path=None):
+    """The distortion sweep at 4096^3: fp32/fp64 x Gaussian/Laplacian/uniform x
+    sym/asym x W 2, 3 x targets 20..80 dB.  One JSON record per run: effective
+    GFLOP/s of the whole path (mean of two timed runs after one warm-up), the W
+    the planner chose, predicted and measured SNR against the fp64 product."""
+    import torch
+    from paper_1110_5765_gb300 import build as b
+    b.build()
+    import paper_1110_5765_gb300 as tdg
+    n = N_SIZE
+    flops = 2.0 * n ** 3
+    recs = []
+    for dtype, T, tt in (("f32", np.float32, torch.float32), ("f64", np.float64, torch.float64)):
+        for kind in ("gaussian", "laplace", "uniform"):
+            A = torch.from_numpy(synth.iid(kind, (n, n), 2001, T)).cuda()
+            B = torch.from_numpy(synth.iid(kind, (n, n), 2002, T)).cuda()
+            ref = torch.matmul(A.double(), B.double())
+            C = torch.empty((n, n), dtype=tt, device="cuda")
+            for form in ("sym", "asym"):
+                for W in (2, 3):
+                    for target in range(20, 81, 10):
+                        p = tdg.Plan(n, n, n, L=L_BLOCK, W=W, dtype=dtype, form=form,
+                                     target_snr_db=float(target))
+                        t = _time(lambda: p.run(A, B, C), torch, reps=2)
+                        info = p.info()
+                        p.close()
+                        rec = {"dtype": dtype, "source": kind, "form": form, "W_req": W,
+                               "target_db": target, "W_used": info["W_used"],
+                               "pred_snr_db": info["pred_snr_db"],
+                               "snr_db": tdg.snr_db(C, ref), "ms": t * 1e3,
+                               "gflops": flops / t / 1e9}
+                        recs.append(rec)
+                        print(json.dumps(rec), flush=True)
+            del ref
+    if out_path:
+        with open(out_path, "w") as f:
+            json.dump(recs, f)
+    return recs
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -450,7 +502,12 @@ def main():
     ap.add_argument("--profile-case", default=None,
                     help="plain|sym|asym|tc_int|tc_fp8: run a small case three times for ncu")
     ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--sweep", default=None, metavar="OUT.json",
+                    help="run the 4096^3 distortion sweep (168 runs) and write its records")
     args = ap.parse_args()
+    if args.sweep:
+        sweep(args.sweep)
+        return
     if args.profile_case:
         profile_case(args.profile_case, args.size)
         return

@@ -130,8 +130,8 @@ tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB, int64_t M,
  * Give the planner the measured representation-noise RMSE s(R_max, W) of
  * Sec. 4.B / eq. 18 for packing W of this plan's dtype, form and L:
  * s[i] belongs to the R_max level t0 + i, where level t means
- * R_t = floor(2^(t/4|0) * (4 + t%4) / 4); a negative entry marks a level that
- * was not measured.  Host array, copied.  Without a table the planner uses
+ * R_t = ((4 + t mod 4) << (t div 4)) / 4 in integer arithmetic (four levels
+ * per octave); a negative entry marks a level that was not measured.  Host array, copied.  Without a table the planner uses
  * only levels inside the error-free region of Prop. 1 (s = 0).
  */
 tdg_status tdgemm_set_rep_noise(tdgemm_plan_t plan, int W, const double *s, int t0, int n);

@@ -1,5 +1,5 @@
 // Steps (c) and (d): the packed multiply-accumulate on CUDA cores with the
-// unpacking, de-companding and the sum over slabs fused into registers.
+// unpacking, de-companding and the sum over slabs fused into the kernel.
 //
 // Packing puts several integer products into one FP mantissa, so step (c)
 // must run on the FP32 / FP64 FMA pipes (a tensor core would round the
@@ -9,20 +9,27 @@
 //     B operand  [k][n]  (sym: b_bar;  asym / plain: b~ or op(B)),
 // so a warp reads each k-row of a tile as consecutive 16-byte vectors.
 //
-// Per CTA: 256 threads each hold a TM x TN register tile; thread 0 streams
-// (BK x BM) and (BK x BN) boxes into a STAGES-deep shared-memory ring with 2-D
-// TMA (cp.async.bulk.tensor, no multicast) completing on mbarriers, keeping
-// STAGES - 1 tiles in flight.  (A separate producer warp would put three
-// warps on one SM sub-partition and cap registers at 168 per thread; the
-// unpacked accumulators need more.)  For every output the packed product of a slab is an fma
-// chain in ascending k starting at +0 (eqs. 8 / 12); at the slab's end the
-// accumulator is unpacked (eqs. 9-10 or 13-14), scaled by the slab's factor
-// (T)(s_A s_B) and added into a second register tile in ascending slab order
-// (eqs. 5, 2), then reset.  That order is the oracle's, so results are
-// bit-identical to it even beyond the error-free packing region.
+// Per CTA: 256 threads each hold a TM x TN register tile of packed
+// accumulators; thread 0 streams (BK x BM) and (BK x BN) boxes into a
+// STAGES-deep shared-memory ring with 2-D TMA (cp.async.bulk.tensor, no
+// multicast) completing on mbarriers, keeping STAGES - 1 tiles in flight.  (A
+// separate producer warp would put three warps on one SM sub-partition and cap
+// registers at 168 per thread.)  For every output the packed product of a slab
+// is an fma chain in ascending k starting at +0 (eqs. 8 / 12); at the slab's
+// end the accumulator is unpacked (eqs. 9-10 or 13-14), scaled by the slab's
+// factor (T)(s_A s_B) and added into the running de-companded sum in ascending
+// slab order (eqs. 5, 2), then reset.  That order is the oracle's, so results
+// are bit-identical to it even beyond the error-free packing region.
+//
+// Where the running sums live: fp64 kernels keep them in registers.  The fp32
+// kernels keep them in tensor memory (TMEM, 256 KB per SM, otherwise unused by
+// CUDA-core work): at each slab end a thread reads 16 columns of its TMEM lane
+// with tcgen05.ld, adds the unpacked values and writes them back with
+// tcgen05.st.  That halves the registers per thread, so two CTAs share an SM.
+//
 // All waits are bounded (2 s of global time); on expiry the kernel records
-// TDG_ETIMEOUT in the plan, waits (bounded) for its outstanding copies and
-// returns without storing.
+// TDG_ETIMEOUT in the plan, waits (bounded) for its outstanding copies, frees
+// its TMEM and returns without storing.
 #pragma once
 
 #include "tdg_common.cuh"
@@ -59,15 +66,76 @@ __device__ inline double rint_t(double a) { return rint(a); }
 __device__ inline float pow2_t(float, int e) { return scalbnf(1.0f, e); }
 __device__ inline double pow2_t(double, int e) { return scalbn(1.0, e); }
 
+// ---- tensor-memory helpers (CUDA-core use of TMEM: alloc, 16-column ld/st)
+__device__ inline void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ inline void tmem_dealloc(uint32_t base, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols)
+                 : "memory");
+}
+__device__ inline void tmem_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ inline void tmem_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ inline void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ inline void tmem_st16(uint32_t taddr, const float *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+__device__ inline void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__host__ __device__ constexpr int pow2_at_least(int v) {
+    int p = 32;
+    while (p < v) p <<= 1;
+    return p;
+}
+
 template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES>
 struct GemmCfg {
     static constexpr int NT = (BM / TM) * (BN / TN);   // threads (16 x 16)
     static constexpr int RG = TM / 4, CG = TN / 4;     // 4-wide fragment groups
     static constexpr int NCACC = FORM == G_ASYM ? W : 1;
+    // running de-companded sums in TMEM (fp32 packed forms) or registers
+    static constexpr bool TMEMC = FORM != G_PLAIN && sizeof(T) == 4;
+    static constexpr int NC = NCACC * TM * TN;         // sums per thread
+    static constexpr int TMEM_COLS = pow2_at_least(2 * NC);
+    static constexpr int MIN_CTAS = TMEMC ? 2 : 1;
     static constexpr size_t STAGE_A = (size_t)BK * BM * sizeof(T);
     static constexpr size_t STAGE_B = (size_t)BK * BN * sizeof(T);
-    static constexpr size_t SMEM = STAGES * (STAGE_A + STAGE_B) + STAGES * sizeof(uint64_t);
+    static constexpr size_t RING = STAGES * (STAGE_A + STAGE_B) + STAGES * sizeof(uint64_t) + 16;
+    // with 256 TMEM columns per CTA at most two CTAs may share an SM's 512:
+    // reserve enough shared memory that a third never fits
+    static constexpr size_t SMEM = (TMEMC && TMEM_COLS > 128 && RING < 80 * 1024) ? 80 * 1024 : RING;
     static_assert(BM / TM == 16 && BN / TN == 16, "16 x 16 thread grid");
+    static_assert(!TMEMC || NC % 16 == 0, "TMEM sums move in 16-column chunks");
+    static_assert(!TMEMC || 2 * NC <= 256, "TMEM columns per CTA");
 };
 
 // Tile sequence shared by the loads and the math: slab l is split into
@@ -89,11 +157,13 @@ struct SlabWalk {
 };
 
 template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES>
-__global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>::NT, 1)
+__global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>::NT,
+                                  GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>::MIN_CTAS)
     packed_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                        const __grid_constant__ CUtensorMap mapB, const GemmArgs<T> g) {
     using Cfg = GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>;
-    constexpr int RG = Cfg::RG, CG = Cfg::CG;
+    constexpr int RG = Cfg::RG, CG = Cfg::CG, NCACC = Cfg::NCACC;
+    constexpr bool TMEMC = Cfg::TMEMC;
 
     if (g.plan->W != W) return;   // the device planner chose another packing
 
@@ -101,8 +171,10 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
     T *sA = reinterpret_cast<T *>(smem);
     T *sB = reinterpret_cast<T *>(smem + STAGES * Cfg::STAGE_A);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * (Cfg::STAGE_A + Cfg::STAGE_B));
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(full + STAGES);
 
     const int tid = threadIdx.x;
+    const int warp = tid >> 5;
     const long long x0 = (long long)blockIdx.y * BM;   // first A-operand column (m or packed row)
     const long long n0 = (long long)blockIdx.x * BN;
     const SlabWalk<T, FORM> walk{g};
@@ -120,6 +192,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         ++issued;
         if ((++ps) * BK >= walk.len(pl)) { ps = 0; ++pl; }
     };
+    if (TMEMC && warp == 0) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
         fence_barrier_init();
@@ -127,19 +200,30 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         tma_prefetch_desc(&mapB);
         for (int s = 0; s < STAGES; ++s) issue_next();
     }
+    if (TMEMC) tmem_fence_before();
     __syncthreads();
+    if (TMEMC) tmem_fence_after();
+    // this thread's TMEM lane (warps w and w+4 share lanes 32*(w%4) .. +31)
+    // and its NC columns
+    const uint32_t tcol = TMEMC ? *tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) +
+                                      (uint32_t)((warp >> 2) * Cfg::NC)
+                                : 0u;
 
     const int tx = tid % (BN / TN), ty = tid / (BN / TN);
     T acc[TM][TN];
-    T cacc[Cfg::NCACC][TM][TN];
+    T cacc[TMEMC ? 1 : NCACC][TMEMC ? 1 : TM][TMEMC ? 1 : TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            acc[i][j] = T(0);
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    if constexpr (!TMEMC) {
 #pragma unroll
-            for (int d = 0; d < Cfg::NCACC; ++d) cacc[d][i][j] = T(0);
-        }
+        for (int d = 0; d < NCACC; ++d)
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) cacc[d][i][j] = T(0);
+    }
 
     T z = T(1), Q = T(1);
     if (FORM != G_PLAIN) {
@@ -165,6 +249,24 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         long long nc = n0 + hj * (BN / CG) + tx * 4;
         jblk[hj] = (int)min(nc / g.L, (long long)g.nN - 1);
     }
+
+    // global coordinates of fragment element (i, j), digit d
+    auto out_row = [&](int i, int d) -> long long {
+        const long long xr = x0 + (i / 4) * (BM / RG) + ty * 4 + (i % 4);
+        if (FORM == G_ASYM) {
+            const long long ib = xr / g.P, jr = xr % g.P;
+            const long long inblk = jr * W + d;
+            if (inblk >= g.L) return -1;
+            return ib * g.L + inblk;
+        }
+        return xr;
+    };
+    auto out_col = [&](int j) -> long long { return n0 + (j / 4) * (BN / CG) + tx * 4 + (j % 4); };
+    auto store_c = [&](long long row, long long col, T v) {
+        if (row < 0 || row >= g.M || col >= g.N) return;
+        T *p = g.C + row * g.ldc + col;
+        *p = g.beta_zero ? mul_rn(g.alpha, v) : fma_rn(g.alpha, v, mul_rn(g.beta, *p));
+    };
 
     int it = 0;
     bool ok = true;
@@ -215,84 +317,105 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
             }
         }
         if (!ok) break;
-        if (FORM != G_PLAIN) {
-            // ---- slab end: keep (optionally), unpack, de-compand, accumulate
+        if (FORM == G_PLAIN) continue;
+
+        // ---- slab end: keep (optionally), unpack, de-compand, accumulate.
+        // The unpacked values stream through in the order f = e * NCACC + d
+        // (e = i * TN + j the fragment element, d the asymmetric digit).
+        const bool first = l == 0, last = l == nslab - 1;
+        // this slab's de-companding factors, all loads issued before any use:
+        // one per 4-row group (sym: a group never straddles a block) or per
+        // packed row (asym), times one per 4-column group
+        constexpr int PR = FORM == G_ASYM ? TM : RG;
+        T prs[PR][CG];
+        const T *pl_tab = g.pair + (long long)l * g.nM * g.nN;
 #pragma unroll
-            for (int gi = 0; gi < RG; ++gi)
+        for (int pi = 0; pi < PR; ++pi)
 #pragma unroll
-                for (int hj = 0; hj < CG; ++hj)
+            for (int hj = 0; hj < CG; ++hj)
+                prs[pi][hj] = __ldg(pl_tab + (long long)iblk[FORM == G_ASYM ? pi : 4 * pi] * g.nN + jblk[hj]);
+        float v[16];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const T pr = g.pair[((long long)l * g.nM + iblk[gi * 4 + e]) * g.nN +
-                                            jblk[hj]];
+        for (int e = 0; e < TM * TN; ++e) {
+            const int i = e / TN, j = e % TN;
+            const T pr = prs[FORM == G_ASYM ? i : i / 4][j / 4];
+            const T r = acc[i][j];
+            acc[i][j] = T(0);
+            if (g.Rbar) {
+                const long long xr = x0 + (i / 4) * (BM / RG) + ty * 4 + (i % 4);
+                const long long nc = out_col(j);
+                if (xr < g.Mrows && nc < g.N) g.Rbar[((long long)l * g.Mrows + xr) * g.N + nc] = r;
+            }
+            T digit[NCACC];
+            if (FORM == G_SYM) {
+                const T u = rint_t(r);                          // eq. 9
+                const T t = rint_t(mul_rn(z, u));
+                digit[0] = fma_rn(-Q, t, u);                    // eq. 10
+            } else {
+                T x = r;
 #pragma unroll
-                        for (int f = 0; f < 4; ++f) {
-                            const int i = gi * 4 + e, j = hj * 4 + f;
-                            T r = acc[i][j];
-                            if (g.Rbar) {
-                                long long xr = x0 + gi * (BM / RG) + ty * 4 + e;
-                                long long nc = n0 + hj * (BN / CG) + tx * 4 + f;
-                                if (xr < g.Mrows && nc < g.N)
-                                    g.Rbar[((long long)l * g.Mrows + xr) * g.N + nc] = r;
-                            }
-                            if (FORM == G_SYM) {
-                                const T u = rint_t(r);                      // eq. 9
-                                const T t = rint_t(mul_rn(z, u));
-                                const T rt = fma_rn(-Q, t, u);              // eq. 10
-                                cacc[0][i][j] = fma_rn(rt, pr, cacc[0][i][j]);
-                            } else {
-                                T x = r;
-#pragma unroll
-                                for (int d = 0; d < W; ++d) {               // eqs. 13-14
-                                    const T rt = rint_t(x);
-                                    cacc[d][i][j] = fma_rn(rt, pr, cacc[d][i][j]);
-                                    if (d + 1 < W) x = mul_rn(Q, sub_rn(x, rt));
-                                }
-                            }
-                            acc[i][j] = T(0);
-                        }
+                for (int d = 0; d < NCACC; ++d) {               // eqs. 13-14
+                    digit[d] = rint_t(x);
+                    if (d + 1 < NCACC) x = mul_rn(Q, sub_rn(x, digit[d]));
                 }
+            }
+#pragma unroll
+            for (int d = 0; d < NCACC; ++d) {
+                if constexpr (TMEMC) {
+                    const int f = e * NCACC + d, slot = f % 16;
+                    if (slot == 0) {
+                        if (first) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) v[q] = 0.f;
+                        } else {
+                            tmem_ld16(tcol + (uint32_t)f, v);
+                        }
+                    }
+                    v[slot] = fma_rn((float)digit[d], (float)pr, v[slot]);
+                    if (slot == 15) {
+                        if (last) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const int fq = f - 15 + q;
+                                const int eq = fq / NCACC, dq = fq % NCACC;
+                                store_c(out_row(eq / TN, dq), out_col(eq % TN), (T)v[q]);
+                            }
+                        } else {
+                            tmem_st16(tcol + (uint32_t)(f - 15), v);
+                        }
+                    }
+                } else {
+                    cacc[d][i][j] = fma_rn(digit[d], pr, cacc[d][i][j]);
+                }
+            }
         }
+        if constexpr (TMEMC) tmem_wait_st();
     }
+
     if (!ok) {
         // let every copy this CTA issued land before it exits
         if (tid == 0)
             for (int k = it; k < issued; ++k) mbar_wait_bounded(&full[k % STAGES], (k / STAGES) & 1);
-        return;
-    }
-
-    // ---------------------------------------------------------------- store C
+    } else if constexpr (!TMEMC) {
+        // ------------------------------------------------------------ store C
 #pragma unroll
-    for (int gi = 0; gi < RG; ++gi)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const long long xr = x0 + gi * (BM / RG) + ty * 4 + e;
+            for (int d = 0; d < NCACC; ++d) {
+                const long long row = out_row(i, d);
 #pragma unroll
-            for (int d = 0; d < Cfg::NCACC; ++d) {
-                long long row;
-                if (FORM == G_ASYM) {
-                    const long long ib = xr / g.P, jr = xr % g.P;
-                    const long long inblk = jr * W + d;
-                    if (inblk >= g.L) continue;
-                    row = ib * g.L + inblk;
-                } else {
-                    row = xr;
-                }
-                if (row >= g.M) continue;
-                T *crow = g.C + row * g.ldc;
-#pragma unroll
-                for (int hj = 0; hj < CG; ++hj)
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) {
-                        const long long nc = n0 + hj * (BN / CG) + tx * 4 + f;
-                        if (nc >= g.N) continue;
-                        const T v = FORM == G_PLAIN ? acc[gi * 4 + e][hj * 4 + f]
-                                                    : cacc[d][gi * 4 + e][hj * 4 + f];
-                        crow[nc] = g.beta_zero ? mul_rn(g.alpha, v)
-                                               : fma_rn(g.alpha, v, mul_rn(g.beta, crow[nc]));
-                    }
+                for (int j = 0; j < TN; ++j)
+                    store_c(row, out_col(j), FORM == G_PLAIN ? acc[i][j] : cacc[d][i][j]);
             }
+    }
+    if constexpr (TMEMC) {
+        tmem_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tmem_fence_after();
+            tmem_dealloc(*tmem_slot, Cfg::TMEM_COLS);
         }
+    }
 }
 
 template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES>

@@ -1,29 +1,36 @@
 // fp32 instantiations of the packed GEMM (sGEMM forms of Sec. 7).
 #include "tdg_gemm.cuh"
+#include "tdg_gemm_tiles.h"
 
 namespace tdg {
+
+template <int FORM, int W, typename C>
+static cudaError_t go(const GemmArgs<float> &g, const CUtensorMap &a, const CUtensorMap &b,
+                      cudaStream_t st) {
+    return launch_cfg<float, FORM, W, C::BM, C::BN, C::TM, C::TN, C::BK, C::STAGES>(g, a, b, st);
+}
 
 template <>
 cudaError_t launch_packed_gemm<float>(int form, int W, const GemmArgs<float> &g,
                                       const CUtensorMap &mapA, const CUtensorMap &mapB,
                                       cudaStream_t st) {
-    // plain / symmetric: 128 x 128 tiles, 8 x 8 per thread
-    // asymmetric: 64 packed rows x 128 columns, 4 x 8 per thread (W result rows each)
-    if (form == G_PLAIN) return launch_cfg<float, G_PLAIN, 1, 128, 128, 8, 8, 16, 6>(g, mapA, mapB, st);
+    using S = TilesF32;
+    using A = TilesF32Asym;
+    if (form == G_PLAIN) return go<G_PLAIN, 1, S>(g, mapA, mapB, st);
     if (form == G_SYM) {
         switch (W) {
-            case 1: return launch_cfg<float, G_SYM, 1, 128, 128, 8, 8, 16, 6>(g, mapA, mapB, st);
-            case 2: return launch_cfg<float, G_SYM, 2, 128, 128, 8, 8, 16, 6>(g, mapA, mapB, st);
-            case 3: return launch_cfg<float, G_SYM, 3, 128, 128, 8, 8, 16, 6>(g, mapA, mapB, st);
-            case 4: return launch_cfg<float, G_SYM, 4, 128, 128, 8, 8, 16, 6>(g, mapA, mapB, st);
+            case 1: return go<G_SYM, 1, S>(g, mapA, mapB, st);
+            case 2: return go<G_SYM, 2, S>(g, mapA, mapB, st);
+            case 3: return go<G_SYM, 3, S>(g, mapA, mapB, st);
+            case 4: return go<G_SYM, 4, S>(g, mapA, mapB, st);
         }
     }
     if (form == G_ASYM) {
         switch (W) {
-            case 1: return launch_cfg<float, G_ASYM, 1, 64, 128, 4, 8, 16, 6>(g, mapA, mapB, st);
-            case 2: return launch_cfg<float, G_ASYM, 2, 64, 128, 4, 8, 16, 6>(g, mapA, mapB, st);
-            case 3: return launch_cfg<float, G_ASYM, 3, 64, 128, 4, 8, 16, 6>(g, mapA, mapB, st);
-            case 4: return launch_cfg<float, G_ASYM, 4, 64, 128, 4, 8, 16, 6>(g, mapA, mapB, st);
+            case 1: return go<G_ASYM, 1, A>(g, mapA, mapB, st);
+            case 2: return go<G_ASYM, 2, A>(g, mapA, mapB, st);
+            case 3: return go<G_ASYM, 3, A>(g, mapA, mapB, st);
+            case 4: return go<G_ASYM, 4, A>(g, mapA, mapB, st);
         }
     }
     return cudaErrorNotSupported;

@@ -1,38 +1,51 @@
-// fp64 instantiations of the packed GEMM (dGEMM forms of Sec. 7).
+// fp64 instantiations of the packed GEMM (dGEMM forms of Sec. 7), and the TMA
+// box shapes every packed-GEMM launch needs.
 #include "tdg_gemm.cuh"
+#include "tdg_gemm_tiles.h"
 
 namespace tdg {
+
+template <int FORM, int W, typename C>
+static cudaError_t go(const GemmArgs<double> &g, const CUtensorMap &a, const CUtensorMap &b,
+                      cudaStream_t st) {
+    return launch_cfg<double, FORM, W, C::BM, C::BN, C::TM, C::TN, C::BK, C::STAGES>(g, a, b, st);
+}
 
 template <>
 cudaError_t launch_packed_gemm<double>(int form, int W, const GemmArgs<double> &g,
                                        const CUtensorMap &mapA, const CUtensorMap &mapB,
                                        cudaStream_t st) {
-    // 64 x 64 tiles, 4 x 4 per thread (asymmetric: 64 packed rows, W result rows each)
-    if (form == G_PLAIN) return launch_cfg<double, G_PLAIN, 1, 64, 64, 4, 4, 16, 4>(g, mapA, mapB, st);
+    using D = TilesF64;
+    if (form == G_PLAIN) return go<G_PLAIN, 1, D>(g, mapA, mapB, st);
     if (form == G_SYM) {
         switch (W) {
-            case 1: return launch_cfg<double, G_SYM, 1, 64, 64, 4, 4, 16, 4>(g, mapA, mapB, st);
-            case 2: return launch_cfg<double, G_SYM, 2, 64, 64, 4, 4, 16, 4>(g, mapA, mapB, st);
-            case 3: return launch_cfg<double, G_SYM, 3, 64, 64, 4, 4, 16, 4>(g, mapA, mapB, st);
-            case 4: return launch_cfg<double, G_SYM, 4, 64, 64, 4, 4, 16, 4>(g, mapA, mapB, st);
+            case 1: return go<G_SYM, 1, D>(g, mapA, mapB, st);
+            case 2: return go<G_SYM, 2, D>(g, mapA, mapB, st);
+            case 3: return go<G_SYM, 3, D>(g, mapA, mapB, st);
+            case 4: return go<G_SYM, 4, D>(g, mapA, mapB, st);
         }
     }
     if (form == G_ASYM) {
         switch (W) {
-            case 1: return launch_cfg<double, G_ASYM, 1, 64, 64, 4, 4, 16, 4>(g, mapA, mapB, st);
-            case 2: return launch_cfg<double, G_ASYM, 2, 64, 64, 4, 4, 16, 4>(g, mapA, mapB, st);
-            case 3: return launch_cfg<double, G_ASYM, 3, 64, 64, 4, 4, 16, 4>(g, mapA, mapB, st);
-            case 4: return launch_cfg<double, G_ASYM, 4, 64, 64, 4, 4, 16, 4>(g, mapA, mapB, st);
+            case 1: return go<G_ASYM, 1, D>(g, mapA, mapB, st);
+            case 2: return go<G_ASYM, 2, D>(g, mapA, mapB, st);
+            case 3: return go<G_ASYM, 3, D>(g, mapA, mapB, st);
+            case 4: return go<G_ASYM, 4, D>(g, mapA, mapB, st);
         }
     }
     return cudaErrorNotSupported;
 }
 
+// TMA boxes {BM, BK} for A and {BN, BK} for B, from the same tile table the
+// launches use
 void packed_gemm_boxes(int dtype, int form, int *box_x_a, int *box_x_b, int *bk) {
-    *bk = 16;
-    if (dtype == TDG_F64) { *box_x_a = 64; *box_x_b = 64; return; }
-    *box_x_a = form == G_ASYM ? 64 : 128;
-    *box_x_b = 128;
+    if (dtype == TDG_F64) {
+        *box_x_a = TilesF64::BM; *box_x_b = TilesF64::BN; *bk = TilesF64::BK;
+    } else if (form == G_ASYM) {
+        *box_x_a = TilesF32Asym::BM; *box_x_b = TilesF32Asym::BN; *bk = TilesF32Asym::BK;
+    } else {
+        *box_x_a = TilesF32::BM; *box_x_b = TilesF32::BN; *bk = TilesF32::BK;
+    }
 }
 
 }  // namespace tdg

@@ -1,21 +1,25 @@
 // Steps (a) and (b) on the data: companding and rounding (eq. 3) fused with
 // packing (eqs. 6, 7, 11) in one pass over each input.
 //
-// Each CTA stages a tile of op(X) in shared memory with loads that are
-// coalesced along whichever stored dimension is contiguous, quantizes it on
-// the way in (a~ = rint(fl_T(x * c_T)) with the block's compander), and writes
-// packed numbers by Horner's rule,
+// Every element is quantized as a~ = rint(fl_T(x * c_T)) with its block's
+// compander and the packed number is built by Horner's rule,
 //     acc = d_{W-1};  acc = fma(w, acc, d_i),  i = W-2 .. 0,
-// coalesced along the output's contiguous dimension.  Digits outside the
+// with w = z for eqs. 6 and 11 and w = z^-1 for eq. 7.  Digits outside the
 // L x L block or the matrix are zero (border clean-up, Sec. 2).
 //
-//   pack along k   (eq. 6 with w = z for A, eq. 7 with w = z^-1 for B, and
-//                   W = 1 for the unpacked operands):  out[l P + j][x]
-//   pack along x   (eq. 11, asymmetric A, w = z):       out[k][i P + j]
-//   k-major codes  (tensor-core forms): out[x][k] as integer-valued fp16 or
-//                   as E4M3 (c = 448 / max|x|, round to nearest even,
-//                   saturating)
-// P = ceil(L / W) packed numbers per block (zero digits pad a ragged block).
+//   pack along k   out[l P + j][x]  (eq. 6 for A, eq. 7 for B, W = 1 for the
+//                  unpacked operands and the plain copies):
+//                    - x contiguous in the input: 16-byte vector loads of the
+//                      W digit rows, vector stores, no shared memory;
+//                    - k contiguous in the input: a 32 x 32W tile staged in
+//                      shared memory with vector loads, then written along x.
+//   pack along x   out[k][i P + j]  (eq. 11, asymmetric A), tile staged in
+//                  shared memory.
+//   k-major codes  out[x][k] (tensor-core forms): integer-valued fp16, or E4M3
+//                  (round to nearest even, saturating).
+// P = ceil(L / W) packed numbers per block.  Each kernel first reads the
+// device plan and returns unless the planner chose its packing; the grids are
+// capped and loop over tiles so that such early exits cost little.
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -27,9 +31,8 @@ namespace tdg {
 namespace {
 
 constexpr int TILE = 32;
+constexpr int MAX_CTAS = 152 * 8;
 
-// op(X)[x][k] lives at src[x * sx + k * sk]; its compander (if any) at
-// c[(x / L) * cx + (k / L) * cl].
 template <typename T>
 struct Src {
     const T *p;
@@ -38,15 +41,20 @@ struct Src {
     const T *c;       // nullptr: copy without companding
     long long cx, cl;
     int L;
-    __device__ inline T load_q(long long x, long long k) const {
-        if (x >= X || k >= K) return T(0);
-        T v = p[x * sx + k * sk];
-        if (c == nullptr) return v;
-        T ct = c[(x / L) * cx + (k / L) * cl];
-        if constexpr (sizeof(T) == 4) return rintf(__fmul_rn(v, ct));
-        else return rint(__dmul_rn(v, ct));
-    }
 };
+
+template <typename T>
+__device__ inline T quant(T v, T c, bool compand) {
+    if (!compand) return v;
+    if constexpr (sizeof(T) == 4) return rintf(__fmul_rn(v, c));
+    else return rint(__dmul_rn(v, c));
+}
+
+template <typename T>
+__device__ inline T fma_t(T a, T b, T c) {
+    if constexpr (sizeof(T) == 4) return __fmaf_rn(a, b, c);
+    else return __fma_rn(a, b, c);
+}
 
 // w = z = 2^-q (wsign < 0) or z^-1 = 2^q (wsign > 0), q from the device plan
 template <typename T>
@@ -57,135 +65,251 @@ __device__ inline T pack_weight(const DevPlan *plan, int wsign) {
 }
 
 template <typename T>
-__device__ inline T fma_t(T a, T b, T c) {
-    if constexpr (sizeof(T) == 4) return __fmaf_rn(a, b, c);
-    else return __fma_rn(a, b, c);
-}
+struct VecT;
+template <>
+struct VecT<float> { static constexpr int n = 4; };
+template <>
+struct VecT<double> { static constexpr int n = 2; };
 
-// Load a (nx x nk) region of op(X) starting at (x0, k0) into s[xr][kc]
-// (row pitch `pitch`), coalescing along the contiguous stored dimension.
-// Elements at or beyond (xlim, klim) are zero.
 template <typename T>
-__device__ inline void stage_tile(const Src<T> &S, T *s, int pitch, long long x0, long long k0,
-                                  int nx, int nk, long long xlim, long long klim) {
-    const int n = nx * nk;
-    if (S.sk == 1) {
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            int xr = e / nk, kc = e % nk;
-            long long x = x0 + xr, k = k0 + kc;
-            s[xr * pitch + kc] = (x < xlim && k < klim) ? S.load_q(x, k) : T(0);
-        }
+__device__ inline void vload(const T *p, T *o) {
+    if constexpr (sizeof(T) == 4) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
     } else {
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            int kc = e / nx, xr = e % nx;
-            long long x = x0 + xr, k = k0 + kc;
-            s[xr * pitch + kc] = (x < xlim && k < klim) ? S.load_q(x, k) : T(0);
+        double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+        o[0] = v.x; o[1] = v.y;
+    }
+}
+
+template <typename T>
+__device__ inline void vstore(T *p, const T *o) {
+    if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    else *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+}
+
+// ------------------------------------------------------------------ pack along k,
+// x contiguous in the input: one item = VEC consecutive x of one packed row
+template <typename T, int W>
+__global__ void __launch_bounds__(256) pack_k_xc_kernel(Src<T> S, int P, const DevPlan *plan,
+                                                        int expectW, int wsign, T *out,
+                                                        long long ldo, long long rows_out,
+                                                        int vec_ok) {
+    if (plan->W != expectW) return;
+    constexpr int VEC = VecT<T>::n;
+    const T w = W > 1 ? pack_weight<T>(plan, wsign) : T(1);
+    const bool compand = S.c != nullptr;
+    const int L = S.L;
+    const long long nx = (S.X + VEC - 1) / VEC;
+    const long long items = rows_out * nx;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const long long row = it / nx;                 // l * P + j
+        const long long x = (it - row * nx) * VEC;
+        const int l = (int)(row / P), j = (int)(row - (long long)l * P);
+        const long long kbase = (long long)l * L + (long long)W * j;
+        const long long klim = min((long long)(l + 1) * L, S.K);
+        const T c = compand ? S.c[(x / L) * S.cx + (long long)l * S.cl] : T(1);
+        T acc[VEC];
+        const bool full = vec_ok && x + VEC <= S.X;
+#pragma unroll
+        for (int i = W - 1; i >= 0; --i) {
+            const long long k = kbase + i;
+            T d[VEC];
+            if (k < klim && W * j + i < L) {
+                const T *src = S.p + k * S.sk + x;
+                if (full) {
+                    vload(src, d);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) d[e] = (x + e < S.X) ? src[e] : T(0);
+                }
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) d[e] = quant(d[e], c, compand);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) d[e] = T(0);
+            }
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) acc[e] = (i == W - 1) ? d[e] : fma_t(w, acc[e], d[e]);
+        }
+        T *dst = out + row * ldo + x;
+        if (full) {
+            vstore(dst, acc);
+        } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (x + e < S.X) dst[e] = acc[e];
         }
     }
 }
 
-// out[l*P + j][x] for j in [j0, j0 + 32), x in [x0, x0 + 32)
+// ------------------------------------------------------------------ pack along k,
+// k contiguous in the input: 32 x-rows x 32 packed columns per tile
 template <typename T, int W>
-__global__ void __launch_bounds__(256) pack_k_kernel(Src<T> S, int P, const DevPlan *plan,
-                                                     int expectW, int wsign, T *out,
-                                                     long long ldo, long long rows_out) {
-    if (plan->W != expectW) return;   // the device planner chose another packing
+__global__ void __launch_bounds__(256) pack_k_kc_kernel(Src<T> S, int P, const DevPlan *plan,
+                                                        int expectW, int wsign, T *out,
+                                                        long long ldo, long long rows_out,
+                                                        int vec_ok) {
+    if (plan->W != expectW) return;
+    constexpr int VEC = VecT<T>::n;
+    constexpr int NK = TILE * W;            // k values per tile row
+    constexpr int PITCH = NK + 1;
+    __shared__ T s[TILE * PITCH];
+    __shared__ T crow[TILE];
     const T w = W > 1 ? pack_weight<T>(plan, wsign) : T(1);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *s = reinterpret_cast<T *>(smem_raw);
-    const int pitch = TILE * W + 1;
+    const bool compand = S.c != nullptr;
     const int L = S.L;
-    const int jt = cdiv_i(P, TILE);
-    const long long l = blockIdx.y / jt;
-    const int j0 = (blockIdx.y % jt) * TILE;
-    const long long x0 = (long long)blockIdx.x * TILE;
-    const long long kslab0 = l * L;
-    const long long klim = min(kslab0 + L, S.K);   // digits stop at the block edge
-    const long long k0 = kslab0 + (long long)W * j0;
-    stage_tile(S, s, pitch, x0, k0, TILE, TILE * W, S.X, klim);
-    __syncthreads();
-    for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-        int jr = e / TILE, xr = e % TILE;
-        int j = j0 + jr;
-        long long x = x0 + xr;
-        if (j >= P || x >= S.X || l * P + j >= rows_out) continue;
-        const T *d = s + xr * pitch + jr * W;
-        T acc = d[W - 1];
+    const int jt = (P + TILE - 1) / TILE;
+    const long long xt = (S.X + TILE - 1) / TILE;
+    const int nK = (int)((S.K + L - 1) / L);
+    const long long tiles = xt * nK * jt;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const long long xtile = t % xt;
+        const long long r = t / xt;
+        const int l = (int)(r / jt), j0 = (int)(r % jt) * TILE;
+        const long long x0 = xtile * TILE;
+        const long long kslab = (long long)l * L;
+        const long long k0 = kslab + (long long)W * j0;
+        const long long klim = min(kslab + L, S.K);
+        __syncthreads();   // previous tile's readers are done with s / crow
+        if (threadIdx.x < TILE) {
+            const long long x = x0 + threadIdx.x;
+            crow[threadIdx.x] = (compand && x < S.X) ? S.c[(x / L) * S.cx + (long long)l * S.cl] : T(1);
+        }
+        __syncthreads();
+        constexpr int CH = NK / VEC;
+        for (int e = threadIdx.x; e < TILE * CH; e += blockDim.x) {
+            const int xr = e / CH, kc = (e % CH) * VEC;
+            const long long x = x0 + xr, k = k0 + kc;
+            T d[VEC];
+            if (x < S.X && vec_ok && k + VEC <= klim) {
+                vload(S.p + x * S.sx + k, d);
+            } else {
 #pragma unroll
-        for (int i = W - 2; i >= 0; --i) acc = fma_t(w, acc, d[i]);
-        out[(l * P + j) * ldo + x] = acc;
+                for (int q = 0; q < VEC; ++q)
+                    d[q] = (x < S.X && k + q < klim) ? S.p[x * S.sx + k + q] : T(0);
+            }
+            const T c = crow[xr];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                const bool valid = x < S.X && k + q < klim;
+                s[xr * PITCH + kc + q] = valid ? quant(d[q], c, compand) : T(0);
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+            const int jr = e / TILE, xr = e % TILE;
+            const int j = j0 + jr;
+            const long long x = x0 + xr;
+            const long long row = (long long)l * P + j;
+            if (j >= P || x >= S.X || row >= rows_out) continue;
+            const T *d = s + xr * PITCH + jr * W;
+            T acc = d[W - 1];
+#pragma unroll
+            for (int i = W - 2; i >= 0; --i) acc = fma_t(w, acc, d[i]);
+            out[row * ldo + x] = acc;
+        }
     }
 }
 
+// ------------------------------------------------------------------ pack along x
 // out[k][i*P + j] for j in [j0, j0 + 32) of row block i, k in [k0, k0 + 32)
 template <typename T, int W>
 __global__ void __launch_bounds__(256) pack_x_kernel(Src<T> S, int P, const DevPlan *plan,
                                                      int expectW, int wsign, T *out,
                                                      long long ldo) {
     if (plan->W != expectW) return;
+    constexpr int NX = TILE * W;
+    constexpr int PITCH = TILE + 1;
+    __shared__ T s[NX * PITCH];
+    __shared__ T ccol[TILE];
     const T w = W > 1 ? pack_weight<T>(plan, wsign) : T(1);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *s = reinterpret_cast<T *>(smem_raw);
-    const int pitch = TILE + 1;
+    const bool compand = S.c != nullptr;
     const int L = S.L;
-    const int jt = cdiv_i(P, TILE);
-    const long long i = blockIdx.x / jt;
-    const int j0 = (blockIdx.x % jt) * TILE;
-    const long long k0 = (long long)blockIdx.y * TILE;
-    const long long xblk0 = i * L;
-    const long long xlim = min(xblk0 + L, S.X);
-    const long long x0 = xblk0 + (long long)W * j0;
-    stage_tile(S, s, pitch, x0, k0, TILE * W, TILE, xlim, S.K);
-    __syncthreads();
-    for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-        int kr = e / TILE, jr = e % TILE;
-        int j = j0 + jr;
-        long long k = k0 + kr;
-        if (j >= P || k >= S.K) continue;
-        const T *d = s + (jr * W) * pitch + kr;
-        T acc = d[(W - 1) * pitch];
+    const int jt = (P + TILE - 1) / TILE;
+    const int nM = (int)((S.X + L - 1) / L);
+    const long long kt = (S.K + TILE - 1) / TILE;
+    const long long tiles = (long long)nM * jt * kt;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const long long ktile = t % kt;
+        const long long r = t / kt;
+        const int i = (int)(r / jt), j0 = (int)(r % jt) * TILE;
+        const long long k0 = ktile * TILE;
+        const long long xblk0 = (long long)i * L;
+        const long long xlim = min(xblk0 + L, S.X);
+        const long long x0 = xblk0 + (long long)W * j0;
+        __syncthreads();
+        if (threadIdx.x < TILE) {
+            const long long k = k0 + threadIdx.x;
+            ccol[threadIdx.x] = (compand && k < S.K) ? S.c[(long long)i * S.cx + (k / L) * S.cl] : T(1);
+        }
+        __syncthreads();
+        if (S.sk == 1) {
+            for (int e = threadIdx.x; e < NX * TILE; e += blockDim.x) {
+                const int xr = e / TILE, kc = e % TILE;
+                const long long x = x0 + xr, k = k0 + kc;
+                const bool valid = x < xlim && k < S.K;
+                s[xr * PITCH + kc] = valid ? quant(S.p[x * S.sx + k], ccol[kc], compand) : T(0);
+            }
+        } else {
+            for (int e = threadIdx.x; e < NX * TILE; e += blockDim.x) {
+                const int kc = e / NX, xr = e % NX;
+                const long long x = x0 + xr, k = k0 + kc;
+                const bool valid = x < xlim && k < S.K;
+                s[xr * PITCH + kc] = valid ? quant(S.p[x + k * S.sk], ccol[kc], compand) : T(0);
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+            const int kr = e / TILE, jr = e % TILE;
+            const int j = j0 + jr;
+            const long long k = k0 + kr;
+            if (j >= P || k >= S.K) continue;
+            const T *d = s + (jr * W) * PITCH + kr;
+            T acc = d[(W - 1) * PITCH];
 #pragma unroll
-        for (int ii = W - 2; ii >= 0; --ii) acc = fma_t(w, acc, d[ii * pitch]);
-        out[k * ldo + i * P + j] = acc;
+            for (int ii = W - 2; ii >= 0; --ii) acc = fma_t(w, acc, d[ii * PITCH]);
+            out[k * ldo + (long long)i * P + j] = acc;
+        }
     }
 }
 
-// k-major quantized codes for the tensor-core forms: out[x][k]
+// ------------------------------------------------------------------ k-major codes
+// out[x][k]; a 32 x 32 tile lies inside one L x L block (L % 64 == 0)
 template <int FP8>
 __global__ void __launch_bounds__(256) codes_kernel(Src<float> S, void *out, long long ldo) {
     __shared__ float s[TILE][TILE + 1];
-    const long long x0 = (long long)blockIdx.y * TILE, k0 = (long long)blockIdx.x * TILE;
-    // stage raw products x*c (rounded in fp32); the integer form rounds below
-    if (S.sk == 1) {
-        for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-            int xr = e / TILE, kc = e % TILE;
-            long long x = x0 + xr, k = k0 + kc;
-            float v = 0.f;
-            if (x < S.X && k < S.K)
-                v = __fmul_rn(S.p[x * S.sx + k * S.sk], S.c[(x / S.L) * S.cx + (k / S.L) * S.cl]);
-            s[xr][kc] = v;
-        }
-    } else {
-        for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-            int kc = e / TILE, xr = e % TILE;
-            long long x = x0 + xr, k = k0 + kc;
-            float v = 0.f;
-            if (x < S.X && k < S.K)
-                v = __fmul_rn(S.p[x * S.sx + k * S.sk], S.c[(x / S.L) * S.cx + (k / S.L) * S.cl]);
-            s[xr][kc] = v;
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-        int xr = e / TILE, kc = e % TILE;
-        long long x = x0 + xr, k = k0 + kc;
-        if (x >= S.X || k >= S.K) continue;
-        float v = s[xr][kc];
-        if constexpr (FP8) {
-            __nv_fp8_storage_t b = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
-            reinterpret_cast<uint8_t *>(out)[x * ldo + k] = b;
+    const long long kt = (S.K + TILE - 1) / TILE, xt = (S.X + TILE - 1) / TILE;
+    for (long long t = blockIdx.x; t < kt * xt; t += gridDim.x) {
+        const long long x0 = (t / kt) * TILE, k0 = (t % kt) * TILE;
+        const float c = S.c[(x0 / S.L) * S.cx + (k0 / S.L) * S.cl];
+        __syncthreads();
+        if (S.sk == 1) {
+            for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+                const int xr = e / TILE, kc = e % TILE;
+                const long long x = x0 + xr, k = k0 + kc;
+                s[xr][kc] = (x < S.X && k < S.K) ? __fmul_rn(S.p[x * S.sx + k], c) : 0.f;
+            }
         } else {
-            reinterpret_cast<__half *>(out)[x * ldo + k] = __float2half_rn(rintf(v));
+            for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+                const int kc = e / TILE, xr = e % TILE;
+                const long long x = x0 + xr, k = k0 + kc;
+                s[xr][kc] = (x < S.X && k < S.K) ? __fmul_rn(S.p[x + k * S.sk], c) : 0.f;
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+            const int xr = e / TILE, kc = e % TILE;
+            const long long x = x0 + xr, k = k0 + kc;
+            if (x >= S.X || k >= S.K) continue;
+            const float v = s[xr][kc];
+            if constexpr (FP8) {
+                __nv_fp8_storage_t b = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+                reinterpret_cast<uint8_t *>(out)[x * ldo + k] = b;
+            } else {
+                reinterpret_cast<__half *>(out)[x * ldo + k] = __float2half_rn(rintf(v));
+            }
         }
     }
 }
@@ -198,15 +322,28 @@ Src<T> make_src(const PackOperand<T> &o) {
     return S;
 }
 
+int capped(long long n) { return (int)max(1LL, min(n, (long long)MAX_CTAS)); }
+
 template <typename T, int W>
 cudaError_t launch_pack_k_w(const PackOperand<T> &o, const DevPlan *plan, int expectW, int wsign,
                             T *out, long long ldo, long long rows_out, cudaStream_t st) {
+    constexpr int VEC = VecT<T>::n;
     Src<T> S = make_src(o);
-    int P = (o.L + W - 1) / W;
-    int nK = cdiv_i(o.K, o.L);
-    dim3 grid(cdiv_i(o.X, TILE), nK * cdiv_i(P, TILE));
-    size_t sm = (size_t)TILE * (TILE * W + 1) * sizeof(T);
-    pack_k_kernel<T, W><<<grid, 256, sm, st>>>(S, P, plan, expectW, wsign, out, ldo, rows_out);
+    const int P = (o.L + W - 1) / W;
+    const bool aligned_in = ((uintptr_t)o.src % 16 == 0);
+    const bool aligned_out = ((uintptr_t)out % 16 == 0) && (ldo % VEC == 0);
+    if (o.sx == 1) {
+        const int vec_ok = aligned_in && aligned_out && (o.sk % VEC == 0);
+        const long long items = rows_out * ((o.X + VEC - 1) / VEC);
+        pack_k_xc_kernel<T, W><<<capped((items + 255) / 256), 256, 0, st>>>(
+            S, P, plan, expectW, wsign, out, ldo, rows_out, vec_ok);
+    } else {
+        const int vec_ok = aligned_in && (o.sx % VEC == 0) && o.sk == 1;
+        const long long tiles = ((o.X + TILE - 1) / TILE) * ((o.K + o.L - 1) / o.L) *
+                                ((P + TILE - 1) / TILE);
+        pack_k_kc_kernel<T, W><<<capped(tiles), 256, 0, st>>>(S, P, plan, expectW, wsign, out, ldo,
+                                                              rows_out, vec_ok);
+    }
     return cudaGetLastError();
 }
 
@@ -214,11 +351,10 @@ template <typename T, int W>
 cudaError_t launch_pack_x_w(const PackOperand<T> &o, const DevPlan *plan, int expectW, int wsign,
                             T *out, long long ldo, cudaStream_t st) {
     Src<T> S = make_src(o);
-    int P = (o.L + W - 1) / W;
-    int nM = cdiv_i(o.X, o.L);
-    dim3 grid(nM * cdiv_i(P, TILE), cdiv_i(o.K, TILE));
-    size_t sm = (size_t)(TILE * W) * (TILE + 1) * sizeof(T);
-    pack_x_kernel<T, W><<<grid, 256, sm, st>>>(S, P, plan, expectW, wsign, out, ldo);
+    const int P = (o.L + W - 1) / W;
+    const long long tiles = ((o.X + o.L - 1) / o.L) * ((P + TILE - 1) / TILE) *
+                            ((o.K + TILE - 1) / TILE);
+    pack_x_kernel<T, W><<<capped(tiles), 256, 0, st>>>(S, P, plan, expectW, wsign, out, ldo);
     return cudaGetLastError();
 }
 
@@ -251,19 +387,19 @@ cudaError_t launch_pack_x(const PackOperand<T> &o, int W, const DevPlan *plan, i
 cudaError_t launch_codes(const PackOperand<float> &o, int fp8, void *out, long long ldo,
                          cudaStream_t st) {
     Src<float> S = make_src(o);
-    dim3 grid(cdiv_i(o.K, TILE), cdiv_i(o.X, TILE));
-    if (fp8) codes_kernel<1><<<grid, 256, 0, st>>>(S, out, ldo);
-    else codes_kernel<0><<<grid, 256, 0, st>>>(S, out, ldo);
+    const long long tiles = ((o.K + TILE - 1) / TILE) * ((o.X + TILE - 1) / TILE);
+    if (fp8) codes_kernel<1><<<capped(tiles), 256, 0, st>>>(S, out, ldo);
+    else codes_kernel<0><<<capped(tiles), 256, 0, st>>>(S, out, ldo);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_pack_k<float>(const PackOperand<float> &, int, const DevPlan *, int, int,
                                           float *, long long, long long, cudaStream_t);
-template cudaError_t launch_pack_k<double>(const PackOperand<double> &, int, const DevPlan *, int, int,
-                                          double *, long long, long long, cudaStream_t);
+template cudaError_t launch_pack_k<double>(const PackOperand<double> &, int, const DevPlan *, int,
+                                           int, double *, long long, long long, cudaStream_t);
 template cudaError_t launch_pack_x<float>(const PackOperand<float> &, int, const DevPlan *, int, int,
                                           float *, long long, cudaStream_t);
-template cudaError_t launch_pack_x<double>(const PackOperand<double> &, int, const DevPlan *, int, int,
-                                          double *, long long, cudaStream_t);
+template cudaError_t launch_pack_x<double>(const PackOperand<double> &, int, const DevPlan *, int,
+                                           int, double *, long long, cudaStream_t);
 
 }  // namespace tdg

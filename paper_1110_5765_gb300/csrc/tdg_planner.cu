@@ -64,8 +64,8 @@ __device__ inline double snr_db(double S, double N) {
 }
 
 __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
-    PlanParams pp, const double *__restrict__ mA, const double *__restrict__ eA,
-    const double *__restrict__ mB, const double *__restrict__ eB,
+    PlanParams pp, const double *__restrict__ mA, const double *__restrict__ vA,
+    const double *__restrict__ mB, const double *__restrict__ vB,
     const double *__restrict__ stab, DevPlan *plan) {
     __shared__ double red[4][kPlanThreads];
     __shared__ double best_n[kPlanThreads];
@@ -77,17 +77,14 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
     double S = 0, T1 = 0, T2 = 0, T3 = 0;
     if (pp.mode != MODE_MANUAL) {
         for (int l = tid; l < pp.nK; l += kPlanThreads) {
-            const double kl = (double)min((long long)L, pp.K - (long long)l * L);
             double X = 0, MA = 0, Y = 0, MB = 0;
             for (int i = 0; i < pp.nM; ++i) {
-                double rows = (double)min((long long)L, pp.M - (long long)i * L);
-                X += eA[(long long)i * pp.nK + l] / (rows * kl);
+                X += vA[(long long)i * pp.nK + l];
                 double m = mA[(long long)i * pp.nK + l];
                 MA += m * m;
             }
             for (int j = 0; j < pp.nN; ++j) {
-                double cols = (double)min((long long)L, pp.N - (long long)j * L);
-                Y += eB[(long long)l * pp.nN + j] / (kl * cols);
+                Y += vB[(long long)l * pp.nN + j];
                 double m = mB[(long long)l * pp.nN + j];
                 MB += m * m;
             }

@@ -4,9 +4,9 @@
 // reorder; Sec. 5.B adds sigma.  Here one CTA reads one L x L tile of the
 // stored matrix with 16-byte vector loads (one HBM pass) and produces
 //   max|x|   exact,
-//   sum x^2  fp64 (fp32 inputs: per-thread double-float accumulation of exact
-//            squares, then an fp64 tree), which the planner divides by the
-//            number of valid elements to get sigma^2 about zero.
+//   sigma^2  sum x^2 / (valid elements), about zero; the sum in fp64 (fp32
+//            inputs: per-thread double-float accumulation of exact squares,
+//            then an fp64 tree).
 // Non-finite inputs raise TDG_ENONFINITE in the plan's device status.
 #include "tdg_common.cuh"
 #include "tdg_internal.h"
@@ -17,30 +17,31 @@ namespace {
 
 // max|x| is kept as the largest bit pattern of |x| (for non-negative IEEE
 // values the integer order is the numeric order), which stays on the integer
-// pipe; NaN/Inf are flagged separately.
+// pipe; NaN/Inf are flagged separately.  Each thread keeps one running sum
+// per vector lane so the dependent add chains run side by side.
 struct Acc {
-    float hi, lo;              // fp32 path: double-float sum of squares
-    double d;                  // fp64 path
+    float hi[4], lo[4];        // fp32 path: double-float sums of squares
+    double d[2];               // fp64 path
     unsigned long long mbits;  // bit pattern of the largest |x|
     int bad;
 };
 
-__device__ inline void add_sq(Acc &a, float x) {
+__device__ inline void add_sq(Acc &a, int lane, float x) {
     // exact square as hi + err (TwoProduct), then TwoSum into (hi, lo)
     float p = __fmul_rn(x, x);
     float e = __fmaf_rn(x, x, -p);
-    float t = __fadd_rn(a.hi, p);
-    float bp = __fsub_rn(t, a.hi);
-    float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
-    a.hi = t;
-    a.lo = __fadd_rn(a.lo, __fadd_rn(err, e));
+    float t = __fadd_rn(a.hi[lane], p);
+    float bp = __fsub_rn(t, a.hi[lane]);
+    float err = __fadd_rn(__fsub_rn(a.hi[lane], __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    a.hi[lane] = t;
+    a.lo[lane] = __fadd_rn(a.lo[lane], __fadd_rn(err, e));
     unsigned int b = __float_as_uint(x) & 0x7fffffffu;
     a.mbits = max(a.mbits, (unsigned long long)b);
     a.bad |= (b >= 0x7f800000u);
 }
 
-__device__ inline void add_sq(Acc &a, double x) {
-    a.d = __fma_rn(x, x, a.d);
+__device__ inline void add_sq(Acc &a, int lane, double x) {
+    a.d[lane & 1] = __fma_rn(x, x, a.d[lane & 1]);
     unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
     a.mbits = max(a.mbits, b);
     a.bad |= (b >= 0x7ff0000000000000ull);
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) block_stats_kernel(const T *__restrict__ 
                                                           long long rows_s, long long cols_s,
                                                           long long ld, int L, int trans,
                                                           int nbc_op, double *__restrict__ mx,
-                                                          double *__restrict__ ss,
+                                                          double *__restrict__ var,
                                                           DevPlan *plan) {
     constexpr int VEC = 16 / sizeof(T);
     const int bj = blockIdx.x, bi = blockIdx.y;
@@ -61,24 +62,31 @@ __global__ void __launch_bounds__(256) block_stats_kernel(const T *__restrict__ 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const bool vec_ok = (ld % VEC == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
 
-    Acc a{0.f, 0.f, 0.0, 0ull, 0};
+    Acc a{{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, {0.0, 0.0}, 0ull, 0};
     for (int r = warp; r < rn; r += nwarp) {
         const T *row = X + (r0 + r) * ld + c0;
         for (int c = lane * VEC; c < cn; c += 32 * VEC) {
             if (vec_ok && c + VEC <= cn) {
                 if constexpr (sizeof(T) == 4) {
                     float4 v = __ldg(reinterpret_cast<const float4 *>(row + c));
-                    add_sq(a, v.x); add_sq(a, v.y); add_sq(a, v.z); add_sq(a, v.w);
+                    add_sq(a, 0, v.x); add_sq(a, 1, v.y); add_sq(a, 2, v.z); add_sq(a, 3, v.w);
                 } else {
                     double2 v = __ldg(reinterpret_cast<const double2 *>(row + c));
-                    add_sq(a, v.x); add_sq(a, v.y);
+                    add_sq(a, 0, v.x); add_sq(a, 1, v.y);
                 }
             } else {
-                for (int e = 0; e < VEC && c + e < cn; ++e) add_sq(a, row[c + e]);
+                for (int e = 0; e < VEC && c + e < cn; ++e) add_sq(a, 0, row[c + e]);
             }
         }
     }
-    double s = (sizeof(T) == 4) ? (double)a.hi + (double)a.lo : a.d;
+    double s;
+    if (sizeof(T) == 4) {
+        s = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s += (double)a.hi[q] + (double)a.lo[q];
+    } else {
+        s = a.d[0] + a.d[1];
+    }
     double m = (sizeof(T) == 4) ? (double)__uint_as_float((unsigned int)a.mbits)
                                 : __longlong_as_double((long long)a.mbits);
     int bad = a.bad;
@@ -105,7 +113,7 @@ __global__ void __launch_bounds__(256) block_stats_kernel(const T *__restrict__ 
         if (lane == 0) {
             long long idx = trans ? (long long)bj * nbc_op + bi : (long long)bi * nbc_op + bj;
             mx[idx] = m;
-            ss[idx] = s;
+            var[idx] = s / ((double)rn * (double)cn);   // sigma^2 about zero
             if (bad) atomicExch(&plan->nonfinite, 1);
         }
     }
@@ -115,10 +123,10 @@ __global__ void __launch_bounds__(256) block_stats_kernel(const T *__restrict__ 
 
 template <typename T>
 cudaError_t launch_block_stats(const T *X, long long rows_s, long long cols_s, long long ld,
-                               int L, int trans, int nbc_op, double *mx, double *ss,
+                               int L, int trans, int nbc_op, double *mx, double *var,
                                DevPlan *plan, cudaStream_t st) {
     dim3 grid(cdiv_i(cols_s, L), cdiv_i(rows_s, L));
-    block_stats_kernel<T><<<grid, 256, 0, st>>>(X, rows_s, cols_s, ld, L, trans, nbc_op, mx, ss,
+    block_stats_kernel<T><<<grid, 256, 0, st>>>(X, rows_s, cols_s, ld, L, trans, nbc_op, mx, var,
                                                 plan);
     return cudaGetLastError();
 }

@@ -10,7 +10,8 @@
 //
 // C = sum_l (s_A,il s_B,lj) * (A~_l B~_l^T), slabs l of L k-values.
 //
-// CTA tile 128 x 256, one CTA per SM (192 KB of shared memory):
+// CTA tile 128 x 256, one persistent CTA per SM (192 KB of shared memory) that
+// walks its share of the output tiles, the pipeline running on across tiles:
 //   warp 0      allocates 512 TMEM columns; lane 0 streams 128-byte-wide k
 //               boxes of A~ (128 rows) and B~ (256 rows) with 2-D TMA
 //               (128-byte swizzle, no multicast) into a 4-deep ring;
@@ -26,6 +27,8 @@
 // Every wait is bounded (2 s of global time); on expiry the CTA records
 // TDG_ETIMEOUT, drains what it issued (bounded) and frees its TMEM.
 #include <cuda_fp16.h>
+
+#include <algorithm>
 
 #include "tdg_common.cuh"
 #include "tdg_internal.h"
@@ -128,10 +131,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long m0 = (long long)blockIdx.y * BM, n0 = (long long)blockIdx.x * BN;
+    // persistent CTAs: tile k of this CTA is blockIdx.x + k * gridDim.x (row-major
+    // over 128 x 256 output tiles)
+    const int tiles_n = (int)((g.N + BN - 1) / BN), tiles_m = (int)((g.M + BM - 1) / BM);
+    const int ntiles = tiles_n * tiles_m;
+    const int my_tiles =
+        ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int slab_stages = g.L / BK;
     const int nslab = g.nK;
-    const int total = nslab * slab_stages;
+    const int per_tile = nslab * slab_stages;
+    const int total = my_tiles * per_tile;
+    auto tile_origin = [&](int k, long long &m0, long long &n0) {
+        const int t = (int)blockIdx.x + k * (int)gridDim.x;
+        m0 = (long long)(t / tiles_n) * BM;
+        n0 = (long long)(t % tiles_n) * BN;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -171,8 +185,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     break;
                 }
                 if (*(volatile int *)abort_flag) break;
-                const int l = it / slab_stages, ks = it % slab_stages;
+                const int kt = it / per_tile, rem = it % per_tile;
+                const int l = rem / slab_stages, ks = rem % slab_stages;
                 const int kx = l * g.L + ks * BK;
+                long long m0, n0;
+                tile_origin(kt, m0, n0);
                 mbar_arrive_expect_tx(&full[stage], STAGE_A + STAGE_B);
                 tma_load_2d(sA + stage * STAGE_A, &mapA, &full[stage], kx, (int)m0);
                 tma_load_2d(sB + stage * STAGE_B, &mapB, &full[stage], kx, (int)n0);
@@ -186,9 +203,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            for (int l = 0; l < nslab && ok; ++l) {
-                const int b = l & 1;
-                if (l >= 2 && !mbar_wait_bounded(&acc_empty[b], ((l >> 1) + 1) & 1)) {
+            for (int gs = 0; gs < my_tiles * nslab && ok; ++gs) {   // global slab count
+                const int b = gs & 1;
+                if (gs >= 2 && !mbar_wait_bounded(&acc_empty[b], ((gs >> 1) + 1) & 1)) {
                     ok = false;
                     break;
                 }
@@ -211,7 +228,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     mma_commit(&empty[stage]);          // frees the stage when done
                 }
                 if (!ok) break;
-                mma_commit(&acc_full[b]);               // slab l is complete in TMEM
+                mma_commit(&acc_full[b]);               // the slab is complete in TMEM
             }
             if (!ok) {
                 raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);
@@ -225,44 +242,58 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int ew = warp - 2;
         const int quad = warp & 3;                     // TMEM lanes 32*quad .. +31
         const int cgrp = ew >> 2;                      // columns [EPI_COLS*cgrp, +EPI_COLS)
-        const long long row = m0 + quad * 32 + lane;
-        const int iblk = (int)min(row / g.L, (long long)g.nM - 1);
-        float cacc[EPI_COLS];
-#pragma unroll
-        for (int c = 0; c < EPI_COLS; ++c) cacc[c] = 0.f;
+        const long long lstride = (long long)g.nM * g.nN;
         bool ok = true;
-        for (int l = 0; l < nslab; ++l) {
-            const int b = l & 1;
-            if (!mbar_wait_bounded(&acc_full[b], (l >> 1) & 1)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t base =
-                tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN + cgrp * EPI_COLS);
+        for (int kt = 0; kt < my_tiles && ok; ++kt) {
+            long long m0, n0;
+            tile_origin(kt, m0, n0);
+            const long long row = m0 + quad * 32 + lane;
+            const int iblk = (int)min(row / g.L, (long long)g.nM - 1);
+            // the thread's EPI_COLS columns lie in one column block (L % 64 == 0,
+            // column groups 64-aligned), so one factor per slab, fetched a slab ahead
+            const long long col0 = n0 + cgrp * EPI_COLS;
+            const int jblk = (int)min(col0 / g.L, (long long)g.nN - 1);
+            const float *prow = g.pair + (long long)iblk * g.nN + jblk;
+            float pr_next = __ldg(prow);
+            float cacc[EPI_COLS];
 #pragma unroll
-            for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
-                float v[16];
-                tmem_ld16(base + ch * 16, v);
-                const long long col0 = n0 + cgrp * EPI_COLS + ch * 16;
-                const int jblk = (int)min(col0 / g.L, (long long)g.nN - 1);
-                const float pr = g.pair[((long long)l * g.nM + iblk) * g.nN + jblk];
+            for (int c = 0; c < EPI_COLS; ++c) cacc[c] = 0.f;
+            for (int l = 0; l < nslab; ++l) {
+                const int gs = kt * nslab + l;
+                const int b = gs & 1;
+                const float pr = pr_next;
+                if (l + 1 < nslab) pr_next = __ldg(prow + (long long)(l + 1) * lstride);
+                if (!mbar_wait_bounded(&acc_full[b], (gs >> 1) & 1)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t base =
+                    tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN + cgrp * EPI_COLS);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) cacc[ch * 16 + e] = __fmaf_rn(v[e], pr, cacc[ch * 16 + e]);
+                for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
+                    float v[16];
+                    tmem_ld16(base + ch * 16, v);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        cacc[ch * 16 + e] = __fmaf_rn(v[e], pr, cacc[ch * 16 + e]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[b]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            if (!ok) break;
+            if (row < g.M) {
+                float *crow = g.C + row * g.ldc;
+#pragma unroll
+                for (int c = 0; c < EPI_COLS; ++c) {
+                    const long long col = col0 + c;
+                    if (col < g.N)
+                        crow[col] = g.beta_zero ? __fmul_rn(g.alpha, cacc[c])
+                                                : __fmaf_rn(g.alpha, cacc[c], __fmul_rn(g.beta, crow[col]));
+                }
+            }
         }
         if (!ok) {
             raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);
             *abort_flag = 1;
-        } else if (row < g.M) {
-            float *crow = g.C + row * g.ldc;
-#pragma unroll
-            for (int c = 0; c < EPI_COLS; ++c) {
-                const long long col = n0 + cgrp * EPI_COLS + c;
-                if (col < g.N)
-                    crow[col] = g.beta_zero ? __fmul_rn(g.alpha, cacc[c])
-                                            : __fmaf_rn(g.alpha, cacc[c], __fmul_rn(g.beta, crow[col]));
-            }
         }
     }
 
@@ -280,7 +311,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 cudaError_t launch_tc_gemm(int fp8, const TcArgs &a, const CUtensorMap &mapA,
                            const CUtensorMap &mapB, cudaStream_t st) {
-    dim3 grid((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM));
+    static int num_sms = 0;
+    if (!num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (num_sms <= 0) num_sms = 1;
+    }
+    const long long tiles = ((a.N + BN - 1) / BN) * ((a.M + BM - 1) / BM);
+    dim3 grid((unsigned)std::min<long long>(tiles, num_sms));
     if (fp8) {
         static bool set = false;
         if (!set) {

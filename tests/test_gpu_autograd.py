@@ -19,6 +19,8 @@ def ag():
     build.build()
     from paper_1110_5765_gb300 import autograd
     yield autograd
+    for p in autograd._plans.values():
+        assert p.info()["device_status"] == 0
     autograd.clear_plan_cache()
 
 

@@ -36,7 +36,7 @@ def stored(X, trans):
 
 def run_gpu(tdg, A, B, *, L, W, dtype, form, transA="N", transB="N", bits=0, target=math.nan,
             manual=None, keep_packed=False, alpha=1.0, beta=0.0, Cin=None, rep=None,
-            allow_fallback=True):
+            allow_fallback=True, expect_status=0):
     M, K = A.shape
     N = B.shape[1]
     As, Bs = dev(stored(A, transA)), dev(stored(B, transB))
@@ -49,6 +49,7 @@ def run_gpu(tdg, A, B, *, L, W, dtype, form, transA="N", transB="N", bits=0, tar
     p.run(As, Bs, C, alpha, beta)
     torch.cuda.synchronize()
     out = {"C": C.cpu().numpy(), "info": p.info(), "plan": p}
+    assert out["info"]["device_status"] == expect_status, out["info"]
     if keep_packed:
         nK = -(-K // L)
         r = torch.zeros((M, N, nK), dtype=torch.int64, device="cuda")
@@ -214,6 +215,7 @@ def test_target_mode_matches_oracle(tdg, orc, dtype, form, target):
     C = torch.zeros((M, N), dtype=TT[dtype], device="cuda")
     p.run(dev(A), dev(B), C)
     i = p.info()
+    assert i["device_status"] == 0, i
     assert i["W_used"] == ref.plan.W
     if ref.plan.W > 1:
         assert (i["q"], i["gamma_a"], i["gamma_b"], i["level"]) == \
@@ -226,7 +228,7 @@ def test_unreachable_without_fallback(tdg, orc):
     A = synth.gaussian((64, 64), 51, np.float32)
     B = synth.gaussian((64, 64), 52, np.float32)
     g = run_gpu(tdg, A, B, L=64, W=2, dtype="f32", form="sym", target=90.0,
-                allow_fallback=False, rep=None)
+                allow_fallback=False, rep=None, expect_status=5)
     assert g["info"]["device_status"] == 5       # TDG_EUNREACHABLE
     g = run_gpu(tdg, A, B, L=64, W=2, dtype="f32", form="sym", target=90.0, rep=None)
     assert g["info"]["W_used"] == 1 and g["info"]["device_status"] == 0
@@ -237,7 +239,7 @@ def test_nonfinite_input_flagged(tdg):
     A = synth.gaussian((64, 64), 61, np.float32)
     A[3, 5] = np.nan
     B = synth.gaussian((64, 64), 62, np.float32)
-    g = run_gpu(tdg, A, B, L=64, W=2, dtype="f32", form="sym", bits=6)
+    g = run_gpu(tdg, A, B, L=64, W=2, dtype="f32", form="sym", bits=6, expect_status=7)
     assert g["info"]["device_status"] == 7       # TDG_ENONFINITE
 
 

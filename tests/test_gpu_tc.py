@@ -37,6 +37,7 @@ def run_tc(tdg, A, B, *, form, L=128, bits=0, target=math.nan, transA="N", trans
     torch.cuda.synchronize()
     info = p.info()
     p.close()
+    assert info["device_status"] == 0, info
     return C.cpu().numpy(), info
 
 

@@ -1,0 +1,110 @@
+"""The paper's workload shapes through the GPU path, checked against the
+oracle on sampled output tiles (needs a GB300)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def tdg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1110_5765_gb300 import build
+    build.build()
+    import paper_1110_5765_gb300 as t
+    return t
+
+
+def same_bits(a, b):
+    return np.array_equal(np.asarray(a).view(np.uint8), np.asarray(b).view(np.uint8))
+
+
+@pytest.fixture(scope="module")
+def faces():
+    # 10304 pixels (a 112 x 92 face) x 4096 images, pixel mean removed
+    return synth.eigenface_pixels(10304, 4096, 7)
+
+
+@pytest.mark.parametrize("target", [30.0, 50.0])
+def test_eigenface_covariance(tdg, orc, faces, target):
+    """C = X^T X, 4096 x 4096 x 10304 (80 full slabs and a half slab): op(A)
+    through the transpose flag, target SNR 30 / 50 dB, fp32, symmetric W = 2.
+    The plan and two sampled 128 x 128 tiles equal the oracle's."""
+    X = faces
+    Xd = torch.from_numpy(X).cuda()
+    p = tdg.Plan(4096, 4096, 10304, L=128, W=2, dtype="f32", form="sym", target_snr_db=target,
+                 transA="T", lda=4096)
+    C = p.run(Xd, Xd)
+    torch.cuda.synchronize()
+    info = p.info()
+    p.close()
+    assert info["device_status"] == 0, info
+    A_op = np.ascontiguousarray(X.T)
+    st = orc.load_s_table()
+    for (ti, tj) in synth.sample_tiles(32, 32, 2, seed=int(target)):
+        rows, cols = (ti * 128, ti * 128 + 128), (tj * 128, tj * 128 + 128)
+        ref = orc.tdgemm(A_op, X, L=128, W=2, dtype="f32", form="sym", target_db=target,
+                         s_table=st, rows=rows, cols=cols)
+        assert info["W_used"] == ref.plan.W
+        got = C[rows[0]:rows[1], cols[0]:cols[1]].cpu().numpy()
+        assert same_bits(got, ref.C)
+
+
+def test_eigenface_projection(tdg, orc, faces):
+    """Y = X^T U onto 400 orthonormal columns (N = 400 is a ragged 3.1 blocks),
+    fp32 symmetric W = 2 at 30 dB: sampled tiles equal the oracle's."""
+    X = faces
+    g = synth.rng(8).standard_normal((10304, 400))
+    U = np.linalg.qr(g)[0].astype(np.float32)
+    p = tdg.Plan(4096, 400, 10304, L=128, W=2, dtype="f32", form="sym", target_snr_db=30.0,
+                 transA="T", lda=4096)
+    Y = p.run(torch.from_numpy(X).cuda(), torch.from_numpy(U).cuda())
+    torch.cuda.synchronize()
+    p.close()
+    st = orc.load_s_table()
+    A_op = np.ascontiguousarray(X.T)
+    for (ti, tj) in [(0, 3), (17, 1)]:
+        rows, cols = (ti * 128, ti * 128 + 128), (tj * 128, min(tj * 128 + 128, 400))
+        ref = orc.tdgemm(A_op, U, L=128, W=2, dtype="f32", form="sym", target_db=30.0,
+                         s_table=st, rows=rows, cols=cols)
+        got = Y[rows[0]:rows[1], cols[0]:cols[1]].cpu().numpy()
+        assert same_bits(got, ref.C)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("kind", ["gaussian", "laplace", "uniform"])
+def test_distortion_sweep_points(tdg, orc, dtype, kind):
+    """A slice of the distortion sweep at 1024^3 (both forms, W 2 and 3,
+    targets 20 and 40 dB): plan decisions equal the oracle's, a sampled tile is
+    bit-identical, and the measured SNR over all of C is within 1 dB of the
+    model's prediction when the packing is error-free, else within 3 dB."""
+    T = np.float32 if dtype == "f32" else np.float64
+    n = 1024
+    A = synth.iid(kind, (n, n), 31, T)
+    B = synth.iid(kind, (n, n), 32, T)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    ref_full = torch.matmul(Ad.double(), Bd.double())
+    st = orc.load_s_table()
+    for form in ("sym", "asym"):
+        for W in (2, 3):
+            for target in (20.0, 40.0):
+                p = tdg.Plan(n, n, n, L=128, W=W, dtype=dtype, form=form, target_snr_db=target)
+                C = p.run(Ad, Bd)
+                info = p.info()
+                p.close()
+                assert info["device_status"] == 0, info
+                ref = orc.tdgemm(A, B, L=128, W=W, dtype=dtype, form=form, target_db=target,
+                                 s_table=st, rows=(256, 384), cols=(640, 768))
+                assert (info["W_used"], info["q"], info["gamma_a"], info["gamma_b"]) == \
+                    (ref.plan.W, ref.plan.q, ref.plan.gA, ref.plan.gB)
+                assert same_bits(C[256:384, 640:768].cpu().numpy(), ref.C)
+                if info["W_used"] > 1:
+                    snr = tdg.snr_db(C, ref_full)
+                    tol = 1.0 if info["W_used"] <= info["w_ef"] else 3.0
+                    assert snr > info["pred_snr_db"] - tol, (form, W, target, snr, info)
