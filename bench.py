@@ -413,6 +413,7 @@ def measure_forms(tdg, torch, A32, B32) -> dict:
         ("tc_int_40dB", dict(dtype="f32", form="tc_int", W=1, target_snr_db=40.0), A32, B32),
         ("tc_fp8", dict(dtype="f32", form="tc_fp8", W=1, bits=0), A32, B32),
     ]
+    out.update(measure_precision_form(tdg, torch))
     for name, kw, A, B in cases:
         try:
             p = tdg.Plan(n, n, n, L=L_BLOCK, **kw)
@@ -489,6 +490,49 @@ def sweep(out_path=None):
         with open(out_path, "w") as f:
             json.dump(recs, f)
     return recs
+
+
+def measure_precision_form(tdg, torch) -> dict:
+    """The precision-form workload: 8192^3 Laplacian(b = 1) fp32, L = 128,
+    tensor-core forms and the packed CUDA-core forms at a 40 dB target, beside
+    cuBLAS fp32 / fp64 on the same GPU."""
+    n = 8192
+    flops = 2.0 * n ** 3
+    A = torch.from_numpy(synth.laplace((n, n), 5001, np.float32)).cuda()
+    B = torch.from_numpy(synth.laplace((n, n), 5002, np.float32)).cuda()
+    ref = torch.matmul(A.double(), B.double())
+    out = {}
+    C32 = torch.empty_like(A)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    t = _time(lambda: torch.matmul(A, B, out=C32), torch)
+    out["p8192_cublas_f32"] = {"gflops": flops / t / 1e9, "ms": t * 1e3, "snr_db": tdg.snr_db(C32, ref)}
+    cases = [("p8192_tc_int_40dB", dict(form="tc_int", W=1, target_snr_db=40.0)),
+             ("p8192_tc_int_8bit", dict(form="tc_int", W=1, bits=8)),
+             ("p8192_tc_fp8", dict(form="tc_fp8", W=1)),
+             ("p8192_sym_f32_W2_40dB", dict(form="sym", W=2, target_snr_db=40.0))]
+    for name, kw in cases:
+        try:
+            p = tdg.Plan(n, n, n, L=L_BLOCK, dtype="f32", **kw)
+            t = _time(lambda: p.run(A, B, C32), torch)
+            info = p.info()
+            out[name] = {"gflops": flops / t / 1e9, "ms": t * 1e3, "snr_db": tdg.snr_db(C32, ref),
+                         "W_used": info["W_used"], "pred_snr_db": info["pred_snr_db"],
+                         "gamma_a": info["gamma_a"], "gamma_b": info["gamma_b"]}
+            p.close()
+        except Exception as e:
+            out[name] = {"error": str(e)[:200]}
+    A64, B64 = A.double(), B.double()
+    C64 = torch.empty_like(A64)
+    t = _time(lambda: torch.matmul(A64, B64, out=C64), torch, reps=1)
+    out["p8192_cublas_f64"] = {"gflops": flops / t / 1e9, "ms": t * 1e3}
+    p = tdg.Plan(n, n, n, L=L_BLOCK, dtype="f64", form="sym", W=3, target_snr_db=40.0)
+    t = _time(lambda: p.run(A64, B64, C64), torch, reps=1)
+    info = p.info()
+    out["p8192_sym_f64_W3_40dB"] = {"gflops": flops / t / 1e9, "ms": t * 1e3,
+                                   "snr_db": tdg.snr_db(C64, ref), "W_used": info["W_used"],
+                                   "pred_snr_db": info["pred_snr_db"]}
+    p.close()
+    return out
 
 
 def main():

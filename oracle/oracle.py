@@ -189,18 +189,29 @@ def aggregates(stA: BlockStats, stB: BlockStats, L: int) -> Aggregates:
     return Aggregates(L * S, T1, T2, T3, L)
 
 
-def model_noise(ag: Aggregates, gA: int, gB: int, s: float) -> float:
+def model_noise(ag: Aggregates, gA: int, gB: int, s: float, rms: bool = False) -> float:
     """Eq. 21 summed over all (i, l, j), with c_A = Gamma_A / m_A per block:
     L sigma_A^2 / (12 c_B^2) + L sigma_B^2 / (12 c_A^2) + L / (144 c_A^2 c_B^2)
-    + s^2 / (c_A c_B)^2."""
+    + s^2 / (c_A c_B)^2.
+
+    ``rms``: s was measured with uniform integers (RMS = max / sqrt(3)); the
+    rounding error of the packed sums grows with their magnitude, i.e. with
+    the RMS of the quantized operands, so scale s by 3 kappa_A kappa_B
+    (kappa = sigma / max per block).  Summed over (i, l, j) the representation
+    term becomes 9 s^2 sum(sigma_A^2 sigma_B^2) / (Gamma_A Gamma_B)^2.  For
+    uniform sources (kappa^2 = 1/3) both forms agree."""
     L = ag.L
+    if not rms:
+        return (L * ag.T1 / (12.0 * gB * gB) + L * ag.T2 / (12.0 * gA * gA)
+                + ag.T3 * (L / 144.0 + s * s) / (float(gA) * gA * float(gB) * gB))
+    g2 = float(gA) * gA * float(gB) * gB
     return (L * ag.T1 / (12.0 * gB * gB) + L * ag.T2 / (12.0 * gA * gA)
-            + ag.T3 * (L / 144.0 + s * s) / (float(gA) * gA * float(gB) * gB))
+            + ag.T3 * (L / 144.0) / g2 + 9.0 * (ag.S / L) * (s * s) / g2)
 
 
-def model_snr_db(ag: Aggregates, gA: int, gB: int, s: float) -> float:
+def model_snr_db(ag: Aggregates, gA: int, gB: int, s: float, rms: bool = False) -> float:
     """Eq. 20 with the noise of ``model_noise``."""
-    N = model_noise(ag, gA, gB, s)
+    N = model_noise(ag, gA, gB, s, rms)
     if N <= 0.0:
         return math.inf
     return 10.0 * math.log10(ag.S / N)
@@ -269,7 +280,8 @@ T_MAX = {"f32": 4 * 24, "f64": 4 * 40}
 
 
 def plan_fixed(bits: int, L: int, W: int, dtype: str, form: str,
-               ag: Aggregates | None = None, st: STable | None = None) -> Plan:
+               ag: Aggregates | None = None, st: STable | None = None,
+               rms: bool = False) -> Plan:
     """Fixed-bit companding: Gamma_A = Gamma_B = 2^(bits-1) - 1, R_max by eq. 17,
     z by eq. 15, the requested W."""
     g = (1 << (bits - 1)) - 1
@@ -284,12 +296,13 @@ def plan_fixed(bits: int, L: int, W: int, dtype: str, form: str,
             if st is not None:
                 t = max(t for t in range(T_MAX[dtype] + 1) if r_level(t) <= R)
                 s = st.get(dtype, form, W, L, t)
-        pl.pred_snr_db = model_snr_db(ag, g, g, s) if s is not None else math.nan
+        pl.pred_snr_db = model_snr_db(ag, g, g, s, rms) if s is not None else math.nan
     return pl
 
 
 def plan_target(ag: Aggregates, L: int, Wreq: int, dtype: str, form: str,
-                target_db: float, st: STable | None, allow_fallback: bool = True) -> Plan:
+                target_db: float, st: STable | None, allow_fallback: bool = True,
+                rms: bool = False) -> Plan:
     """Distortion-controlled choice (Prop. 4 and Sec. 6, uniform W per call):
     for W = Wreq, Wreq-1, ..., 2 take the R_max level maximising the model SNR
     (eq. 27's argmax, ties to the smaller level) with companders split per
@@ -311,7 +324,7 @@ def plan_target(ag: Aggregates, L: int, Wreq: int, dtype: str, form: str,
             s = rep_noise(st, dtype, form, W, L, t, R, q)
             if s is None:
                 continue
-            snr = model_snr_db(ag, gA, gB, s)
+            snr = model_snr_db(ag, gA, gB, s, rms)
             if best is None or snr > best.pred_snr_db:
                 best = Plan(W=W, q=q, gA=gA, gB=gB, R=R, Wef=w_ef(R, q, dtype), t=t,
                             pred_snr_db=snr)
@@ -446,7 +459,8 @@ class Result:
 def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: str,
            bits: int = 0, target_db: float = math.nan, s_table: STable | None = None,
            allow_fallback: bool = True, manual: tuple | None = None,
-           gammas: tuple | None = None, alpha: float = 1.0, beta: float = 0.0, C_in: np.ndarray | None = None,
+           gammas: tuple | None = None, noise_rms: bool = False,
+           alpha: float = 1.0, beta: float = 0.0, C_in: np.ndarray | None = None,
            rows=None, cols=None, want_rint: bool = False, keep_packed: bool = False) -> Result:
     """Companded-and-packed C = alpha op(A) op(B) + beta C on the CPU.
 
@@ -455,7 +469,8 @@ def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: st
     Parameters come from ``bits`` (fixed-bit mode), ``target_db`` (distortion
     target) or ``manual = (q, c_A, c_B)`` (uniform companders, as in the
     measurement protocol of Sec. 4.B) or ``gammas = (Gamma_A, Gamma_B)``
-    (given integer companders).  ``rows``/``cols`` restrict the computed
+    (given integer companders).  ``noise_rms`` selects the RMS-scaled
+    representation noise of ``model_noise``.  ``rows``/``cols`` restrict the computed
     outputs to a window (for asym, row windows must align to L)."""
     T = NP_T[dtype]
     A = np.ascontiguousarray(A, dtype=T)
@@ -489,9 +504,9 @@ def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: st
             pl = Plan(W=W, q=q, gA=gA, gB=gB, R=R, Wef=w_ef(R, q, dtype))
             pl.pred_snr_db = model_snr_db(ag, gA, gB, 0.0) if W <= pl.Wef else math.nan
         elif bits > 0:
-            pl = plan_fixed(bits, L, W, dtype, form, ag, s_table)
+            pl = plan_fixed(bits, L, W, dtype, form, ag, s_table, noise_rms)
         else:
-            pl = plan_target(ag, L, W, dtype, form, target_db, s_table, allow_fallback)
+            pl = plan_target(ag, L, W, dtype, form, target_db, s_table, allow_fallback, noise_rms)
         if pl.W == 1 and pl.gA == 0:
             C = gemm_plain(A, B, dtype, (r0, r1), (c0, c1))
             Cin = None if C_in is None else C_in[r0:r1, c0:c1]

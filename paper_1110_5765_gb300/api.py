@@ -17,7 +17,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import DTYPES, FORMS, TDG_ALLOW_FALLBACK, TDG_KEEP_PACKED, Info, check
+from ._lib import DTYPES, FORMS, TDG_ALLOW_FALLBACK, TDG_KEEP_PACKED, TDG_NOISE_RMS, Info, check
 
 _TORCH_DT = {"f32": torch.float32, "f64": torch.float64}
 _DT_OF = {torch.float32: "f32", torch.float64: "f64"}
@@ -89,7 +89,8 @@ class Plan:
                  form: str = "sym", target_snr_db: float = math.nan, bits: int = 0,
                  transA: str = "N", transB: str = "N", lda: int | None = None,
                  ldb: int | None = None, ldc: int | None = None, allow_fallback: bool = True,
-                 keep_packed: bool = False, rep_noise: str | dict | None = "package"):
+                 keep_packed: bool = False, rep_noise: str | dict | None = "package",
+                 noise_rms: bool = False):
         self._L = _lib.load()
         self.M, self.N, self.K = int(M), int(N), int(K)
         self.L, self.W, self.dtype, self.form = int(L), int(W), dtype, form
@@ -97,7 +98,8 @@ class Plan:
         self.lda = lda if lda is not None else (self.K if transA == "N" else self.M)
         self.ldb = ldb if ldb is not None else (self.N if transB == "N" else self.K)
         self.ldc = ldc if ldc is not None else self.N
-        flags = (TDG_ALLOW_FALLBACK if allow_fallback else 0) | (TDG_KEEP_PACKED if keep_packed else 0)
+        flags = ((TDG_ALLOW_FALLBACK if allow_fallback else 0) | (TDG_KEEP_PACKED if keep_packed else 0)
+                 | (TDG_NOISE_RMS if noise_rms else 0))
         h = ctypes.c_void_p()
         check(self._L.tdgemm_plan(ctypes.byref(h), transA.encode(), transB.encode(), self.M,
                                   self.N, self.K, self.lda, self.ldb, self.ldc, self.L, self.W,

@@ -319,6 +319,7 @@ static PlanParams params_of(const tdgemm_plan_s *p) {
     if (is_tc_form(p->form)) pp.p = 24;
     pp.bits = p->bits;
     pp.allow_fallback = (p->flags & TDG_ALLOW_FALLBACK) ? 1 : 0;
+    pp.noise_rms = (p->flags & TDG_NOISE_RMS) ? 1 : 0;
     pp.target_db = p->target;
     pp.manual_q = p->manual_q; pp.manual_cA = p->manual_cA; pp.manual_cB = p->manual_cB;
     pp.nM = p->nM; pp.nK = p->nK; pp.nN = p->nN;

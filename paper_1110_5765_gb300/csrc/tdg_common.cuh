@@ -42,6 +42,7 @@ struct PlanParams {
     int p;             // mantissa bits of T (24 / 53): u_sys = 2^-p
     int bits;          // fixed-bit mode
     int allow_fallback;
+    int noise_rms;     // representation noise scaled by crest factors
     double target_db;
     int manual_q;
     double manual_cA, manual_cB;

@@ -64,6 +64,27 @@ __device__ inline double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 __device__ inline float rint_t(float a) { return rintf(a); }
 __device__ inline double rint_t(double a) { return rint(a); }
 __device__ inline float pow2_t(float, int e) { return scalbnf(1.0f, e); }
+
+// Round to nearest, ties to even, on the FMA/ALU pipes: for |x| < 2^23,
+// (x + s) - s with s = copysign(2^23, x) rounds x to an integer (the sum has
+// unit spacing and 2^23 is even), and copysign restores the sign of a zero
+// result; larger floats are integers already.  Bit-identical to rintf for
+// every non-NaN float (checked exhaustively over all 2^32 patterns).  The
+// slab epilogue rounds twice per output, where a conversion-pipe rint would
+// issue at a fraction of the FMA rate.
+#ifndef TDG_EPILOGUE_RINT_ALU
+#define TDG_EPILOGUE_RINT_ALU 1
+#endif
+__device__ inline float rint_epi(float x) {
+#if TDG_EPILOGUE_RINT_ALU
+    const float s = copysignf(8388608.0f, x);
+    const float r = copysignf(__fsub_rn(__fadd_rn(x, s), s), x);
+    return fabsf(x) < 8388608.0f ? r : x;
+#else
+    return rintf(x);
+#endif
+}
+__device__ inline double rint_epi(double x) { return rint(x); }
 __device__ inline double pow2_t(double, int e) { return scalbn(1.0, e); }
 
 // ---- tensor-memory helpers (CUDA-core use of TMEM: alloc, 16-column ld/st)
@@ -348,14 +369,14 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
             }
             T digit[NCACC];
             if (FORM == G_SYM) {
-                const T u = rint_t(r);                          // eq. 9
-                const T t = rint_t(mul_rn(z, u));
+                const T u = rint_epi(r);                        // eq. 9
+                const T t = rint_epi(mul_rn(z, u));
                 digit[0] = fma_rn(-Q, t, u);                    // eq. 10
             } else {
                 T x = r;
 #pragma unroll
                 for (int d = 0; d < NCACC; ++d) {               // eqs. 13-14
-                    digit[d] = rint_t(x);
+                    digit[d] = rint_epi(x);
                     if (d + 1 < NCACC) x = mul_rn(Q, sub_rn(x, digit[d]));
                 }
             }

@@ -276,40 +276,95 @@ __global__ void __launch_bounds__(256) pack_x_kernel(Src<T> S, int P, const DevP
 }
 
 // ------------------------------------------------------------------ k-major codes
-// out[x][k]; a 32 x 32 tile lies inside one L x L block (L % 64 == 0)
+// out[x][k] as integer-valued fp16 or E4M3; the compander of a 64 x 64 tile
+// is one value (tiles are 64-aligned and L % 64 == 0)
 template <int FP8>
-__global__ void __launch_bounds__(256) codes_kernel(Src<float> S, void *out, long long ldo) {
-    __shared__ float s[TILE][TILE + 1];
-    const long long kt = (S.K + TILE - 1) / TILE, xt = (S.X + TILE - 1) / TILE;
-    for (long long t = blockIdx.x; t < kt * xt; t += gridDim.x) {
-        const long long x0 = (t / kt) * TILE, k0 = (t % kt) * TILE;
+__device__ inline void encode8(const float *v, unsigned char *dst) {
+    if constexpr (FP8) {
+        uint2 w;
+        uint32_t b[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) b[i] = __nv_cvt_float_to_fp8(v[i], __NV_SATFINITE, __NV_E4M3);
+        w.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+        w.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+        *reinterpret_cast<uint2 *>(dst) = w;
+    } else {
+        __half h[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) h[i] = __float2half_rn(rintf(v[i]));
+        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
+    }
+}
+
+// k contiguous in the input: one item = 8 consecutive k of one row x
+template <int FP8>
+__global__ void __launch_bounds__(256) codes_kc_kernel(Src<float> S, unsigned char *out,
+                                                       long long ldo, int vec_ok) {
+    constexpr int ES = FP8 ? 1 : 2;
+    const long long nk8 = (S.K + 7) / 8;
+    const long long items = S.X * nk8;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const long long x = it / nk8, k = (it - x * nk8) * 8;
+        const float c = S.c[(x / S.L) * S.cx + (k / S.L) * S.cl];
+        const float *src = S.p + x * S.sx + k;
+        float v[8];
+        if (vec_ok && k + 8 <= S.K) {
+            float4 a = __ldg(reinterpret_cast<const float4 *>(src));
+            float4 b = __ldg(reinterpret_cast<const float4 *>(src + 4));
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = (k + i < S.K) ? src[i] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __fmul_rn(v[i], c);
+        unsigned char *dst = out + (x * ldo + k) * ES;
+        if (k + 8 <= ldo) {
+            encode8<FP8>(v, dst);   // ldo is padded to 128: the tail lands in padding
+        }
+    }
+}
+
+// x contiguous in the input: 64 x 64 tiles transposed through shared memory
+template <int FP8>
+__global__ void __launch_bounds__(256) codes_xc_kernel(Src<float> S, unsigned char *out,
+                                                       long long ldo, int vec_ok) {
+    constexpr int ES = FP8 ? 1 : 2;
+    constexpr int T64 = 64;
+    constexpr int PITCH = T64 + 4;               // floats
+    __shared__ float s[T64 * PITCH];             // s[x][k]
+    const long long xt = (S.X + T64 - 1) / T64, kt = (S.K + T64 - 1) / T64;
+    for (long long t = blockIdx.x; t < xt * kt; t += gridDim.x) {
+        const long long x0 = (t % xt) * T64, k0 = (t / xt) * T64;
         const float c = S.c[(x0 / S.L) * S.cx + (k0 / S.L) * S.cl];
         __syncthreads();
-        if (S.sk == 1) {
-            for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-                const int xr = e / TILE, kc = e % TILE;
-                const long long x = x0 + xr, k = k0 + kc;
-                s[xr][kc] = (x < S.X && k < S.K) ? __fmul_rn(S.p[x * S.sx + k], c) : 0.f;
+        // load: 64 k-rows x 64 x-values, float4 along x
+        for (int e = threadIdx.x; e < T64 * (T64 / 4); e += blockDim.x) {
+            const int kr = e / (T64 / 4), xc = (e % (T64 / 4)) * 4;
+            const long long k = k0 + kr, x = x0 + xc;
+            float v[4];
+            if (k < S.K && vec_ok && x + 4 <= S.X) {
+                float4 a = __ldg(reinterpret_cast<const float4 *>(S.p + k * S.sk + x));
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = (k < S.K && x + i < S.X) ? S.p[k * S.sk + x + i] : 0.f;
             }
-        } else {
-            for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-                const int kc = e / TILE, xr = e % TILE;
-                const long long x = x0 + xr, k = k0 + kc;
-                s[xr][kc] = (x < S.X && k < S.K) ? __fmul_rn(S.p[x + k * S.sk], c) : 0.f;
-            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s[(xc + i) * PITCH + kr] = __fmul_rn(v[i], c);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-            const int xr = e / TILE, kc = e % TILE;
+        // store: rows x, 8 k per thread
+        for (int e = threadIdx.x; e < T64 * (T64 / 8); e += blockDim.x) {
+            const int xr = e / (T64 / 8), kc = (e % (T64 / 8)) * 8;
             const long long x = x0 + xr, k = k0 + kc;
-            if (x >= S.X || k >= S.K) continue;
-            const float v = s[xr][kc];
-            if constexpr (FP8) {
-                __nv_fp8_storage_t b = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
-                reinterpret_cast<uint8_t *>(out)[x * ldo + k] = b;
-            } else {
-                reinterpret_cast<__half *>(out)[x * ldo + k] = __float2half_rn(rintf(v));
-            }
+            if (x >= S.X || k >= ldo) continue;
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = (k + i < S.K) ? s[xr * PITCH + kc + i] : 0.f;
+            encode8<FP8>(v, out + (x * ldo + k) * ES);
         }
     }
 }
@@ -387,9 +442,21 @@ cudaError_t launch_pack_x(const PackOperand<T> &o, int W, const DevPlan *plan, i
 cudaError_t launch_codes(const PackOperand<float> &o, int fp8, void *out, long long ldo,
                          cudaStream_t st) {
     Src<float> S = make_src(o);
-    const long long tiles = ((o.K + TILE - 1) / TILE) * ((o.X + TILE - 1) / TILE);
-    if (fp8) codes_kernel<1><<<capped(tiles), 256, 0, st>>>(S, out, ldo);
-    else codes_kernel<0><<<capped(tiles), 256, 0, st>>>(S, out, ldo);
+    unsigned char *ob = reinterpret_cast<unsigned char *>(out);
+    const bool aligned = ((uintptr_t)o.src % 16 == 0) && ((uintptr_t)out % 16 == 0) && ldo % 8 == 0;
+    if (o.sk == 1) {
+        const int vec_ok = aligned && (o.sx % 4 == 0);
+        const long long items = o.X * ((o.K + 7) / 8);
+        const int g = capped((items + 255) / 256);
+        if (fp8) codes_kc_kernel<1><<<g, 256, 0, st>>>(S, ob, ldo, vec_ok);
+        else codes_kc_kernel<0><<<g, 256, 0, st>>>(S, ob, ldo, vec_ok);
+    } else {
+        const int vec_ok = aligned && o.sx == 1 && (o.sk % 4 == 0);
+        const long long tiles = ((o.X + 63) / 64) * ((o.K + 63) / 64);
+        const int g = capped(tiles);
+        if (fp8) codes_xc_kernel<1><<<g, 256, 0, st>>>(S, ob, ldo, vec_ok);
+        else codes_xc_kernel<0><<<g, 256, 0, st>>>(S, ob, ldo, vec_ok);
+    }
     return cudaGetLastError();
 }
 

@@ -50,13 +50,21 @@ __device__ inline void split_gammas(long long R, int L, double rho, int &gA, int
     gB = (int)min(b, (long long)INT32_MAX);
 }
 
-// eq. 21 summed over (i, l, j); operation order as written above
-__device__ inline double model_noise(const DevPlan &a, int L, double gA, double gB, double s) {
+// eq. 21 summed over (i, l, j); operation order as written above.  With rms
+// the representation term is scaled by the blocks' crest factors (s measured
+// on uniform integers, RMS = max / sqrt(3)): 9 s^2 sum(sigma_A^2 sigma_B^2).
+__device__ inline double model_noise(const DevPlan &a, int L, double gA, double gB, double s,
+                                     int rms) {
     double t1 = __ddiv_rn(__dmul_rn((double)L, a.T1), __dmul_rn(__dmul_rn(12.0, gB), gB));
     double t2 = __ddiv_rn(__dmul_rn((double)L, a.T2), __dmul_rn(__dmul_rn(12.0, gA), gA));
-    double t3 = __ddiv_rn(__dmul_rn(a.T3, __dadd_rn(__ddiv_rn((double)L, 144.0), __dmul_rn(s, s))),
-                          __dmul_rn(__dmul_rn(__dmul_rn(gA, gA), gB), gB));
-    return __dadd_rn(__dadd_rn(t1, t2), t3);
+    const double g2 = __dmul_rn(__dmul_rn(__dmul_rn(gA, gA), gB), gB);
+    if (!rms) {
+        double t3 = __ddiv_rn(__dmul_rn(a.T3, __dadd_rn(__ddiv_rn((double)L, 144.0), __dmul_rn(s, s))), g2);
+        return __dadd_rn(__dadd_rn(t1, t2), t3);
+    }
+    double t3 = __ddiv_rn(__dmul_rn(a.T3, __ddiv_rn((double)L, 144.0)), g2);
+    double t4 = __ddiv_rn(__dmul_rn(__dmul_rn(9.0, __ddiv_rn(a.S, (double)L)), __dmul_rn(s, s)), g2);
+    return __dadd_rn(__dadd_rn(__dadd_rn(t1, t2), t3), t4);
 }
 
 __device__ inline double snr_db(double S, double N) {
@@ -126,7 +134,7 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
         }
         a.W = 1; a.gA = gA; a.gB = gB; a.R = (long long)L * gA * gB;
         a.q = q_for(a.R); a.Wef = w_ef(a.R, a.q, pp.p);
-        a.pred_snr = snr_db(a.S, model_noise(a, L, gA, gB, 0.0));
+        a.pred_snr = snr_db(a.S, model_noise(a, L, gA, gB, 0.0, pp.noise_rms));
         if (pp.mode == MODE_TARGET && a.pred_snr < pp.target_db) a.status = TDG_EUNREACHABLE;
     } else if (pp.mode == MODE_MANUAL) {
         a.W = pp.Wreq; a.q = pp.manual_q; a.gA = a.gB = 0; a.R = 0; a.Wef = 0;
@@ -144,7 +152,7 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
             if (tbest >= pp.t0 && tbest < pp.t0 + pp.nt)
                 s = stab[(pp.Wreq - 2) * pp.nt + (tbest - pp.t0)];
         }
-        if (s >= 0.0) a.pred_snr = snr_db(a.S, model_noise(a, L, g, g, s));
+        if (s >= 0.0) a.pred_snr = snr_db(a.S, model_noise(a, L, g, g, s, pp.noise_rms));
     } else {  // MODE_TARGET, packed forms
         int t_lo = 0;
         while (r_level(t_lo) < L) ++t_lo;
@@ -169,7 +177,7 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
                     s = stab[(W - 2) * pp.nt + (t - pp.t0)];
                 }
                 if (s < 0.0) continue;
-                double n = model_noise(a, L, gA, gB, s);
+                double n = model_noise(a, L, gA, gB, s, pp.noise_rms);
                 if (n < bn) { bn = n; bt = t; }
             }
             best_n[tid] = bn;

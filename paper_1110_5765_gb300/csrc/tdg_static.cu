@@ -160,7 +160,7 @@ tdg_status run_static(bool nA, bool nB, long long M, long long N, long long K, l
     PlanParams pp{};
     pp.mode = MODE_FIXED; pp.form = form; pp.dtype = sizeof(T) == 8 ? TDG_F64 : TDG_F32;
     pp.L = L; pp.Wreq = W; pp.p = sizeof(T) == 8 ? 53 : 24; pp.bits = bits;
-    pp.allow_fallback = 0; pp.target_db = NAN;
+    pp.allow_fallback = 0; pp.noise_rms = 0; pp.target_db = NAN;
     pp.nM = nM; pp.nK = nK; pp.nN = nN; pp.M = M; pp.N = N; pp.K = K;
     pp.t0 = 0; pp.nt = 0;
     ST_TRY(launch_planner<T>(pp, mA, eA, mB, eB, nullptr, dplan, cA, sA, cB, sB, pair, st));

@@ -56,27 +56,41 @@ __global__ void __launch_bounds__(256) block_stats_kernel(const T *__restrict__ 
                                                           DevPlan *plan) {
     constexpr int VEC = 16 / sizeof(T);
     const int bj = blockIdx.x, bi = blockIdx.y;
-    const long long r0 = (long long)bi * L, c0 = (long long)bj * L;
-    const int rn = (int)min((long long)L, rows_s - r0);
+    const long long r0b = (long long)bi * L, c0 = (long long)bj * L;
+    const int rn = (int)min((long long)L, rows_s - r0b);
     const int cn = (int)min((long long)L, cols_s - c0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const bool vec_ok = (ld % VEC == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
 
     Acc a{{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, {0.0, 0.0}, 0ull, 0};
-    for (int r = warp; r < rn; r += nwarp) {
-        const T *row = X + (r0 + r) * ld + c0;
-        for (int c = lane * VEC; c < cn; c += 32 * VEC) {
-            if (vec_ok && c + VEC <= cn) {
-                if constexpr (sizeof(T) == 4) {
-                    float4 v = __ldg(reinterpret_cast<const float4 *>(row + c));
-                    add_sq(a, 0, v.x); add_sq(a, 1, v.y); add_sq(a, 2, v.z); add_sq(a, 3, v.w);
+    // rows in batches of four per warp so four 16-byte loads are in flight
+    // before any of them is consumed
+    constexpr int RB = 4;
+    for (int c = lane * VEC; c < cn; c += 32 * VEC) {
+        const bool vec = vec_ok && c + VEC <= cn;
+        for (int r0 = warp; r0 < rn; r0 += RB * nwarp) {
+            T v[RB][VEC];
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                const int r = r0 + u * nwarp;
+                const T *row = X + (r0b + r) * ld + c0 + c;
+                if (r < rn && vec) {
+                    if constexpr (sizeof(T) == 4) {
+                        float4 q = __ldg(reinterpret_cast<const float4 *>(row));
+                        v[u][0] = q.x; v[u][1] = q.y; v[u][2] = q.z; v[u][3] = q.w;
+                    } else {
+                        double2 q = __ldg(reinterpret_cast<const double2 *>(row));
+                        v[u][0] = q.x; v[u][1] = q.y;
+                    }
                 } else {
-                    double2 v = __ldg(reinterpret_cast<const double2 *>(row + c));
-                    add_sq(a, 0, v.x); add_sq(a, 1, v.y);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) v[u][e] = (r < rn && c + e < cn) ? row[e] : T(0);
                 }
-            } else {
-                for (int e = 0; e < VEC && c + e < cn; ++e) add_sq(a, 0, row[c + e]);
             }
+#pragma unroll
+            for (int u = 0; u < RB; ++u)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) add_sq(a, e, v[u][e]);
         }
     }
     double s;

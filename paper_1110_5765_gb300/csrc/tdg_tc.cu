@@ -282,12 +282,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             if (!ok) break;
             if (row < g.M) {
                 float *crow = g.C + row * g.ldc;
+                const bool vec = ((g.ldc & 3) == 0) && (((uintptr_t)g.C & 15) == 0);
 #pragma unroll
-                for (int c = 0; c < EPI_COLS; ++c) {
+                for (int c = 0; c < EPI_COLS; c += 4) {
                     const long long col = col0 + c;
-                    if (col < g.N)
-                        crow[col] = g.beta_zero ? __fmul_rn(g.alpha, cacc[c])
-                                                : __fmaf_rn(g.alpha, cacc[c], __fmul_rn(g.beta, crow[col]));
+                    float o[4];
+                    if (vec && col + 4 <= g.N) {
+                        if (g.beta_zero) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) o[q] = __fmul_rn(g.alpha, cacc[c + q]);
+                        } else {
+                            const float4 in = *reinterpret_cast<const float4 *>(crow + col);
+                            const float iv[4] = {in.x, in.y, in.z, in.w};
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                o[q] = __fmaf_rn(g.alpha, cacc[c + q], __fmul_rn(g.beta, iv[q]));
+                        }
+                        *reinterpret_cast<float4 *>(crow + col) = make_float4(o[0], o[1], o[2], o[3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (col + q < g.N)
+                                crow[col + q] = g.beta_zero
+                                                    ? __fmul_rn(g.alpha, cacc[c + q])
+                                                    : __fmaf_rn(g.alpha, cacc[c + q], __fmul_rn(g.beta, crow[col + q]));
+                    }
                 }
             }
         }

@@ -200,16 +200,19 @@ def _synthetic_table(orc, dtype, form, L, Wmax):
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("form", ["sym", "asym"])
 @pytest.mark.parametrize("target", [10.0, 30.0, 60.0])
-def test_target_mode_matches_oracle(tdg, orc, dtype, form, target):
+@pytest.mark.parametrize("rms", [False, True])
+def test_target_mode_matches_oracle(tdg, orc, dtype, form, target, rms):
     T = NP[dtype]
     L = 64
     A = 3.0 * synth.uniform((192, 256), 41, T)
     B = synth.laplace((256, 160), 42, T)
     st, dense = _synthetic_table(orc, dtype, form, L, 3)
-    ref = orc.tdgemm(A, B, L=L, W=3, dtype=dtype, form=form, target_db=target, s_table=st)
+    ref = orc.tdgemm(A, B, L=L, W=3, dtype=dtype, form=form, target_db=target, s_table=st,
+                     noise_rms=rms)
     M, K = A.shape
     N = B.shape[1]
-    p = tdg.Plan(M, N, K, L=L, W=3, dtype=dtype, form=form, target_snr_db=target, rep_noise=None)
+    p = tdg.Plan(M, N, K, L=L, W=3, dtype=dtype, form=form, target_snr_db=target, rep_noise=None,
+                 noise_rms=rms)
     for W in (2, 3):
         p.set_rep_noise(W, dense[W], 0)
     C = torch.zeros((M, N), dtype=TT[dtype], device="cuda")
