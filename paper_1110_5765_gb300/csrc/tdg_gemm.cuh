@@ -69,11 +69,10 @@ __device__ inline float pow2_t(float, int e) { return scalbnf(1.0f, e); }
 // (x + s) - s with s = copysign(2^23, x) rounds x to an integer (the sum has
 // unit spacing and 2^23 is even), and copysign restores the sign of a zero
 // result; larger floats are integers already.  Bit-identical to rintf for
-// every non-NaN float (checked exhaustively over all 2^32 patterns).  The
-// slab epilogue rounds twice per output, where a conversion-pipe rint would
-// issue at a fraction of the FMA rate.
+// every non-NaN float (checked exhaustively over all 2^32 patterns).  Kept as
+// an option: on GB300 the native rint measured faster in the slab epilogue.
 #ifndef TDG_EPILOGUE_RINT_ALU
-#define TDG_EPILOGUE_RINT_ALU 1
+#define TDG_EPILOGUE_RINT_ALU 0   // measured slower than the native rint on GB300
 #endif
 __device__ inline float rint_epi(float x) {
 #if TDG_EPILOGUE_RINT_ALU
@@ -177,7 +176,8 @@ struct SlabWalk {
     }
 };
 
-template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES>
+template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES,
+          bool KEEP>
 __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>::NT,
                                   GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>::MIN_CTAS)
     packed_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         // ---- slab end: keep (optionally), unpack, de-compand, accumulate.
         // The unpacked values stream through in the order f = e * NCACC + d
         // (e = i * TN + j the fragment element, d the asymmetric digit).
-        const bool first = l == 0, last = l == nslab - 1;
+        const bool first = l == 0;
         // this slab's de-companding factors, all loads issued before any use:
         // one per 4-row group (sym: a group never straddles a block) or per
         // packed row (asym), times one per 4-column group
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
             const T pr = prs[FORM == G_ASYM ? i : i / 4][j / 4];
             const T r = acc[i][j];
             acc[i][j] = T(0);
-            if (g.Rbar) {
+            if constexpr (KEEP) {
                 const long long xr = x0 + (i / 4) * (BM / RG) + ty * 4 + (i % 4);
                 const long long nc = out_col(j);
                 if (xr < g.Mrows && nc < g.N) g.Rbar[((long long)l * g.Mrows + xr) * g.N + nc] = r;
@@ -393,18 +393,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
                         }
                     }
                     v[slot] = fma_rn((float)digit[d], (float)pr, v[slot]);
-                    if (slot == 15) {
-                        if (last) {
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) {
-                                const int fq = f - 15 + q;
-                                const int eq = fq / NCACC, dq = fq % NCACC;
-                                store_c(out_row(eq / TN, dq), out_col(eq % TN), (T)v[q]);
-                            }
-                        } else {
-                            tmem_st16(tcol + (uint32_t)(f - 15), v);
-                        }
-                    }
+                    if (slot == 15) tmem_st16(tcol + (uint32_t)(f - 15), v);
                 } else {
                     cacc[d][i][j] = fma_rn(digit[d], pr, cacc[d][i][j]);
                 }
@@ -417,7 +406,21 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         // let every copy this CTA issued land before it exits
         if (tid == 0)
             for (int k = it; k < issued; ++k) mbar_wait_bounded(&full[k % STAGES], (k / STAGES) & 1);
-    } else if constexpr (!TMEMC) {
+    } else if constexpr (TMEMC) {
+        // ------------------------------------------------------------ store C
+        // from the running sums in TMEM, 16 columns at a time (kept out of
+        // the slab loop so its code stays small)
+#pragma unroll
+        for (int f0 = 0; f0 < Cfg::NC; f0 += 16) {
+            float v[16];
+            tmem_ld16(tcol + (uint32_t)f0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int eq = (f0 + q) / NCACC, dq = (f0 + q) % NCACC;
+                store_c(out_row(eq / TN, dq), out_col(eq % TN), (T)v[q]);
+            }
+        }
+    } else {
         // ------------------------------------------------------------ store C
 #pragma unroll
         for (int i = 0; i < TM; ++i)
@@ -439,11 +442,12 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
     }
 }
 
-template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES>
-cudaError_t launch_cfg(const GemmArgs<T> &g, const CUtensorMap &mapA, const CUtensorMap &mapB,
-                       cudaStream_t st) {
+template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES,
+          bool KEEP>
+cudaError_t launch_keep(const GemmArgs<T> &g, const CUtensorMap &mapA, const CUtensorMap &mapB,
+                        cudaStream_t st) {
     using Cfg = GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>;
-    auto kern = packed_gemm_kernel<T, FORM, W, BM, BN, TM, TN, BK, STAGES>;
+    auto kern = packed_gemm_kernel<T, FORM, W, BM, BN, TM, TN, BK, STAGES, KEEP>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
@@ -454,6 +458,16 @@ cudaError_t launch_cfg(const GemmArgs<T> &g, const CUtensorMap &mapA, const CUte
     dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.Mrows + BM - 1) / BM));
     kern<<<grid, Cfg::NT, Cfg::SMEM, st>>>(mapA, mapB, g);
     return cudaGetLastError();
+}
+
+// KEEP (store every packed slab result for tdgemm_unpack) is a separate
+// instantiation so the usual kernel carries none of that code.
+template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES>
+cudaError_t launch_cfg(const GemmArgs<T> &g, const CUtensorMap &mapA, const CUtensorMap &mapB,
+                       cudaStream_t st) {
+    if (FORM != G_PLAIN && g.Rbar)
+        return launch_keep<T, FORM, W, BM, BN, TM, TN, BK, STAGES, true>(g, mapA, mapB, st);
+    return launch_keep<T, FORM, W, BM, BN, TM, TN, BK, STAGES, false>(g, mapA, mapB, st);
 }
 
 }  // namespace tdg
