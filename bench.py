@@ -492,6 +492,46 @@ def sweep(out_path=None):
     return recs
 
 
+def kernel_control_sweep(out_path=None):
+    """Throughput control over inner kernels (Sec. 6, Fig. 7's experiment):
+    4096^3 fp32, inputs uniform on [-max_e, max_e] with max_e drawn per L x L
+    block from {4, ..., 2048} (the paper's generic test matrices, L = 128
+    here), symmetric packing planned for a 20 dB target, and the fraction of
+    accelerated inner kernels raised from 0 to 1 in steps of 0.1.  One JSON
+    record per point: effective GFLOP/s of the whole path (mean of three timed
+    runs after one warm-up) and the SNR against the fp64 product."""
+    import torch
+    from paper_1110_5765_gb300 import build as b
+    b.build()
+    import paper_1110_5765_gb300 as tdg
+    n = N_SIZE
+    flops = 2.0 * n ** 3
+    A = torch.from_numpy(synth.blockwise_range_uniform((n, n), 3001, L_BLOCK, np.float32)).cuda()
+    B = torch.from_numpy(synth.blockwise_range_uniform((n, n), 3002, L_BLOCK, np.float32)).cuda()
+    ref = torch.matmul(A.double(), B.double())
+    C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    recs = []
+    p = tdg.Plan(n, n, n, L=L_BLOCK, W=W_PACK, dtype="f32", form="sym", target_snr_db=TARGET_DB)
+    t = _time(lambda: p.run(A, B, C), torch)
+    recs.append({"control": "off", "ms": t * 1e3, "gflops": flops / t / 1e9,
+                 "snr_db": tdg.snr_db(C, ref), "W_used": p.info()["W_used"]})
+    print(json.dumps(recs[-1]), flush=True)
+    for k in range(11):
+        F = k / 10.0
+        p.set_kernel_control("fraction", F)
+        t = _time(lambda: p.run(A, B, C), torch)
+        m = p.kernel_mask()
+        recs.append({"control": "fraction", "F": F, "accelerated": int(m.sum()),
+                     "kernels": int(m.size), "ms": t * 1e3, "gflops": flops / t / 1e9,
+                     "snr_db": tdg.snr_db(C, ref)})
+        print(json.dumps(recs[-1]), flush=True)
+    p.close()
+    if out_path:
+        with open(out_path, "w") as f:
+            json.dump(recs, f)
+    return recs
+
+
 def measure_precision_form(tdg, torch) -> dict:
     """The precision-form workload: 8192^3 Laplacian(b = 1) fp32, L = 128,
     tensor-core forms and the packed CUDA-core forms at a 40 dB target, beside
@@ -548,7 +588,12 @@ def main():
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--sweep", default=None, metavar="OUT.json",
                     help="run the 4096^3 distortion sweep (168 runs) and write its records")
+    ap.add_argument("--fig7", default=None, metavar="OUT.json",
+                    help="run the 4096^3 inner-kernel throughput-control sweep (Sec. 6)")
     args = ap.parse_args()
+    if args.fig7:
+        kernel_control_sweep(args.fig7)
+        return
     if args.sweep:
         sweep(args.sweep)
         return

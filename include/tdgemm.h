@@ -150,6 +150,39 @@ tdg_status tdgemm_set_rep_noise(tdgemm_plan_t plan, int W, const double *s, int 
 tdg_status tdgemm_set_manual(tdgemm_plan_t plan, int q, double c_a, double c_b);
 
 /*
+ * Throughput-distortion control over inner kernels (Sec. 6).  Inner kernel
+ * (i, j) is the L x L output block C_ij = sum_l A_il B_lj.  With control on,
+ * each call of tdgemm_quantize_pack predicts, from the block statistics and
+ * the companders the planner chose, the ratio S_ij / N_ij of that inner
+ * kernel (the noise model of eq. 19 restricted to its K / L block products,
+ * representation noise s of the chosen packing as in the plan's options) and
+ * accelerates (packs) only some of them; tdgemm_gemm computes the rest with
+ * the conventional product (W = 1), so the output is exact there.
+ *
+ *   mode 0   control off (every inner kernel follows the plan; default)
+ *   mode 1   SNR threshold: accelerate the inner kernels whose predicted
+ *            10 log10(S_ij / N_ij) >= value (dB)
+ *   mode 2   fraction: accelerate the ceil(value * nM * nN) inner kernels
+ *            of highest predicted S_ij / N_ij (ties to the lower row-major
+ *            index); value in [0, 1]
+ *
+ * Valid for the SYM form with a planned (fixed-bit or target) plan, at most
+ * 16384 inner kernels, and L a multiple of the GEMM CTA tile (128 for fp32,
+ * 64 for fp64).  A plan whose planner fell back to W = 1 accelerates nothing.
+ * TDG_EINVAL otherwise.  Allocates the mask, ratio and plain-operand buffers
+ * on the first call that turns control on; they are freed with the plan.
+ */
+tdg_status tdgemm_set_kernel_control(tdgemm_plan_t plan, int mode, double value);
+
+/*
+ * Copy the inner-kernel mask of the last tdgemm_quantize_pack to host memory:
+ * out[i * nN + j] = 1 where inner kernel (i, j) is accelerated, else 0;
+ * n >= nM * nN bytes.  Synchronises the plan's last stream.  TDG_ESTATE when
+ * control is off or nothing was packed.
+ */
+tdg_status tdgemm_kernel_mask(tdgemm_plan_t plan, uint8_t *out, int64_t n);
+
+/*
  * Steps (a) and (b): block statistics, planner, companders, companding and
  * packing of A and B into the plan's workspace.  A and B are device pointers
  * in the plan's dtype (fp32 for the TC forms).

@@ -297,6 +297,7 @@ def plan_fixed(bits: int, L: int, W: int, dtype: str, form: str,
                 t = max(t for t in range(T_MAX[dtype] + 1) if r_level(t) <= R)
                 s = st.get(dtype, form, W, L, t)
         pl.pred_snr_db = model_snr_db(ag, g, g, s, rms) if s is not None else math.nan
+        pl.extra["s_rep"] = s if s is not None else 0.0
     return pl
 
 
@@ -327,7 +328,7 @@ def plan_target(ag: Aggregates, L: int, Wreq: int, dtype: str, form: str,
             snr = model_snr_db(ag, gA, gB, s, rms)
             if best is None or snr > best.pred_snr_db:
                 best = Plan(W=W, q=q, gA=gA, gB=gB, R=R, Wef=w_ef(R, q, dtype), t=t,
-                            pred_snr_db=snr)
+                            pred_snr_db=snr, extra={"s_rep": s})
         if best is None:
             continue
         if best_overall is None:
@@ -350,6 +351,58 @@ def compander(m: np.ndarray, gamma: int) -> tuple[np.ndarray, np.ndarray]:
     c[nz] = float(gamma) / m[nz]
     s[nz] = 1.0 / c[nz]
     return c, s
+
+
+# --------------------------------------------------------------------------
+# Sec. 6: throughput/distortion control per inner kernel
+# --------------------------------------------------------------------------
+def kernel_ratios(stA: BlockStats, stB: BlockStats, L: int, gA: int, gB: int, s: float,
+                  rms: bool = False) -> np.ndarray:
+    """Predicted signal-to-noise ratio (linear) of every L x L inner kernel
+    R_ij with the call's companders: S_ij = L sum_l sigma_A,il^2 sigma_B,lj^2
+    (the output power of eq. 20) over N_ij = sum_l of the subblock noise of
+    eq. 21, both summed in ascending l."""
+    nM, nK = stA.m.shape
+    nN = stB.m.shape[1]
+    vA, vB = stA.var, stB.var
+    gA2, gB2 = float(gA) * gA, float(gB) * gB
+    out = np.zeros((nM, nN))
+    for i in range(nM):
+        for j in range(nN):
+            S = 0.0
+            N = 0.0
+            for l in range(nK):
+                va, vb = float(vA[i, l]), float(vB[l, j])
+                ma2 = float(stA.m[i, l]) * float(stA.m[i, l])
+                mb2 = float(stB.m[l, j]) * float(stB.m[l, j])
+                S += L * va * vb
+                n = L * va * mb2 / (12.0 * gB2) + L * vb * ma2 / (12.0 * gA2)
+                if rms:
+                    n += ma2 * mb2 * (L / 144.0) / (gA2 * gB2) + 9.0 * va * vb * (s * s) / (gA2 * gB2)
+                else:
+                    n += ma2 * mb2 * (L / 144.0 + s * s) / (gA2 * gB2)
+                N += n
+            out[i, j] = S / N if N > 0.0 else math.inf
+    return out
+
+
+def kernel_mask(ratios: np.ndarray, mode: str, value: float) -> np.ndarray:
+    """Which inner kernels run packed (Sec. 6, one W for the accelerated ones):
+    'snr'      -- those whose predicted SNR meets S_kernel = value dB
+                  (ratio >= 10^(value/10));
+    'fraction' -- throughput control: the ceil(value * T) kernels with the
+                  highest predicted SNR (ties to the lower row-major index)."""
+    T = ratios.size
+    flat = ratios.ravel()
+    if mode == "snr":
+        thr = math.pow(10.0, value / 10.0)
+        return (flat >= thr).reshape(ratios.shape)
+    k = int(math.ceil(value * T))
+    order = sorted(range(T), key=lambda t: (-flat[t], t))
+    m = np.zeros(T, dtype=bool)
+    for t in order[:k]:
+        m[t] = True
+    return m.reshape(ratios.shape)
 
 
 # --------------------------------------------------------------------------
@@ -461,7 +514,8 @@ def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: st
            allow_fallback: bool = True, manual: tuple | None = None,
            gammas: tuple | None = None, noise_rms: bool = False,
            alpha: float = 1.0, beta: float = 0.0, C_in: np.ndarray | None = None,
-           rows=None, cols=None, want_rint: bool = False, keep_packed: bool = False) -> Result:
+           rows=None, cols=None, want_rint: bool = False, keep_packed: bool = False,
+           kernel_control: tuple | None = None) -> Result:
     """Companded-and-packed C = alpha op(A) op(B) + beta C on the CPU.
 
     A is op(A) (M x K), B is op(B) (K x N), both already in T.  ``form`` is
@@ -470,7 +524,9 @@ def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: st
     target) or ``manual = (q, c_A, c_B)`` (uniform companders, as in the
     measurement protocol of Sec. 4.B) or ``gammas = (Gamma_A, Gamma_B)``
     (given integer companders).  ``noise_rms`` selects the RMS-scaled
-    representation noise of ``model_noise``.  ``rows``/``cols`` restrict the computed
+    representation noise of ``model_noise``.  ``kernel_control = (mode,
+    value)`` ('snr' or 'fraction', Sec. 6) computes the inner kernels that
+    ``kernel_mask`` leaves out with the conventional product instead.  ``rows``/``cols`` restrict the computed
     outputs to a window (for asym, row windows must align to L)."""
     T = NP_T[dtype]
     A = np.ascontiguousarray(A, dtype=T)
@@ -542,6 +598,17 @@ def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: st
            _p(Cacc))
     else:
         raise ValueError(form)
+    if kernel_control is not None and form == "sym":
+        s_rep = pl.extra.get("s_rep", 0.0)
+        ratios = kernel_ratios(stA, stB, L, pl.gA, pl.gB, s_rep, noise_rms)
+        mask = kernel_mask(ratios, *kernel_control)
+        pl.extra["kernel_mask"] = mask
+        plain = gemm_plain(A, B, dtype, (r0, r1), (c0, c1))
+        for m in range(r0, r1):
+            for n0 in range(c0, c1, L):
+                if not mask[m // L, n0 // L]:
+                    n1 = min(n0 + L, c1)
+                    Cacc[m - r0, n0 - c0:n1 - c0] = plain[m - r0, n0 - c0:n1 - c0]
     Cin = None if C_in is None else C_in[r0:r1, c0:c1]
     C = epilogue(Cacc, alpha, beta, Cin, dtype)
     res = Result(C, pl, rint, cA, cB, sA, sB)

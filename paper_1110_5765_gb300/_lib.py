@@ -22,7 +22,8 @@ STATUS = {0: "TDG_OK", 1: "TDG_EINVAL", 2: "TDG_ENOMEM", 3: "TDG_ECUDA", 4: "TDG
           5: "TDG_EUNREACHABLE", 6: "TDG_ETIMEOUT", 7: "TDG_ENONFINITE", 8: "TDG_ESTATE"}
 
 # every symbol include/tdgemm.h declares
-EXPORTS = ["tdgemm_plan", "tdgemm_set_rep_noise", "tdgemm_set_manual", "tdgemm_quantize_pack",
+EXPORTS = ["tdgemm_plan", "tdgemm_set_rep_noise", "tdgemm_set_manual",
+           "tdgemm_set_kernel_control", "tdgemm_kernel_mask", "tdgemm_quantize_pack",
            "tdgemm_gemm", "tdgemm_run", "tdgemm_run_host", "tdgemm_unpack", "tdgemm_plan_info",
            "tdgemm_plan_destroy", "tdgemm_snr", "tdgemm_run_static", "tdgemm_last_error",
            "tdgemm_version"]
@@ -58,6 +59,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                               i64, i64, i64, i32, i32, i32, i32, dbl, i32, u32]
     L.tdgemm_set_rep_noise.argtypes = [vp, i32, ctypes.POINTER(dbl), i32, i32]
     L.tdgemm_set_manual.argtypes = [vp, i32, dbl, dbl]
+    L.tdgemm_set_kernel_control.argtypes = [vp, i32, dbl]
+    L.tdgemm_kernel_mask.argtypes = [vp, vp, i64]
     L.tdgemm_quantize_pack.argtypes = [vp, vp, vp, vp]
     L.tdgemm_gemm.argtypes = [vp, vp, dbl, dbl, vp]
     L.tdgemm_run.argtypes = [vp, vp, vp, vp, dbl, dbl, vp]

@@ -123,6 +123,23 @@ class Plan:
     def set_manual(self, q: int, c_a: float = 1.0, c_b: float = 1.0):
         check(self._L.tdgemm_set_manual(self._h, int(q), float(c_a), float(c_b)))
 
+    _KCTRL = {None: 0, "off": 0, "snr": 1, "fraction": 2}
+
+    def set_kernel_control(self, mode: str | None, value: float = 0.0):
+        """Sec. 6 control over inner kernels: mode 'snr' accelerates the L x L
+        output blocks whose predicted SNR (dB) reaches ``value``, 'fraction'
+        the ``ceil(value * nM * nN)`` blocks of highest predicted SNR; the
+        others are computed with the conventional product.  None turns it off."""
+        check(self._L.tdgemm_set_kernel_control(self._h, self._KCTRL[mode], float(value)))
+
+    def kernel_mask(self) -> np.ndarray:
+        """(nM, nN) uint8 mask of the inner kernels the last pack accelerated."""
+        nM = -(-self.M // self.L)
+        nN = -(-self.N // self.L)
+        out = np.zeros(nM * nN, dtype=np.uint8)
+        check(self._L.tdgemm_kernel_mask(self._h, out.ctypes.data, out.size))
+        return out.reshape(nM, nN)
+
     # -- steps
     def _check_operand(self, X: torch.Tensor, trans: str, ld: int, what: str):
         if not X.is_cuda:

@@ -110,6 +110,13 @@ struct tdgemm_plan_s {
     bool have_table = false;
     // host-buffer staging (tdgemm_run_host)
     void *hA = nullptr, *hB = nullptr, *hC = nullptr;
+    // Sec. 6 inner-kernel control (off: kctrl_mode == 0)
+    int kctrl_mode = 0;
+    double kctrl_value = 0.0, kctrl_thr = 0.0;
+    long long kctrl_k = 0;
+    void *kA = nullptr, *kB = nullptr;        // plain k-major copies for unaccelerated kernels
+    double *kratio = nullptr;
+    unsigned char *kmask = nullptr;
     // state
     const void *A_user = nullptr, *B_user = nullptr;
     bool packed = false, gemm_done = false;
@@ -129,7 +136,8 @@ static std::vector<int> candidates(const tdgemm_plan_s *p) {
     if (p->form == TDG_PLAIN || is_tc_form(p->form)) return {1};
     if (p->mode == MODE_TARGET) {
         for (int w = p->W; w >= 2; --w) c.push_back(w);
-        if (p->flags & TDG_ALLOW_FALLBACK) c.push_back(0);   // 0: plain fallback
+        // 0: plain fallback (with Sec. 6 control the masked plain launch covers it)
+        if ((p->flags & TDG_ALLOW_FALLBACK) && !p->kctrl_mode) c.push_back(0);
     } else {
         c.push_back(p->W);
     }
@@ -312,6 +320,53 @@ extern "C" tdg_status tdgemm_set_manual(tdgemm_plan_t p, int q, double c_a, doub
     return TDG_OK;
 }
 
+extern "C" tdg_status tdgemm_set_kernel_control(tdgemm_plan_t p, int mode, double value) {
+    if (!p) return fail(TDG_EINVAL, "plan is NULL");
+    if (mode == 0) { p->kctrl_mode = 0; p->packed = false; return TDG_OK; }
+    if (p->form != TDG_SYM) return fail(TDG_EINVAL, "inner-kernel control needs the SYM form");
+    if (p->mode == MODE_MANUAL) return fail(TDG_EINVAL, "inner-kernel control needs a planned (not manual) plan");
+    if (mode != 1 && mode != 2) return fail(TDG_EINVAL, "mode must be 0, 1 (SNR) or 2 (fraction)");
+    if (!isfinite(value)) return fail(TDG_EINVAL, "value must be finite");
+    if (mode == 2 && (value < 0.0 || value > 1.0)) return fail(TDG_EINVAL, "fraction must be in [0, 1]");
+    for (int gf : {G_SYM, G_PLAIN}) {
+        int bxa, bxb, bk;
+        packed_gemm_boxes(p->dtype, gf, &bxa, &bxb, &bk);
+        if (p->L % bxa || p->L % bxb)
+            return fail(TDG_EINVAL,
+                        "inner-kernel control needs L to be a multiple of the %dx%d CTA tile",
+                        bxa, bxb);
+    }
+    const long long T = (long long)p->nM * p->nN;
+    if (T > 16384) return fail(TDG_EINVAL, "inner-kernel control supports up to 16384 inner kernels");
+    if (!p->kratio) {
+        CU_TRY(cudaMalloc(&p->kratio, (size_t)T * 8));
+        CU_TRY(cudaMalloc(&p->kmask, (size_t)T));
+        CU_TRY(cudaMemset(p->kmask, 0, (size_t)T));
+    }
+    if (!p->kA) {
+        OpShape s = op_shape(p, 0);
+        CU_TRY(cudaMalloc(&p->kA, (size_t)(s.a_rows * s.a_ld) * p->esz));
+        CU_TRY(cudaMalloc(&p->kB, (size_t)(s.b_rows * s.b_ld) * p->esz));
+    }
+    p->kctrl_mode = mode;
+    p->kctrl_value = value;
+    p->kctrl_thr = mode == 1 ? pow(10.0, value / 10.0) : 0.0;
+    p->kctrl_k = mode == 2 ? (long long)ceil(value * (double)T) : 0;
+    p->packed = false;   // the packed operands no longer match: pack again
+    return TDG_OK;
+}
+
+extern "C" tdg_status tdgemm_kernel_mask(tdgemm_plan_t p, uint8_t *out, int64_t n) {
+    if (!p || !out) return fail(TDG_EINVAL, "NULL argument");
+    const long long T = (long long)p->nM * p->nN;
+    if (!p->kctrl_mode || !p->kmask) return fail(TDG_ESTATE, "inner-kernel control is off");
+    if (n < T) return fail(TDG_EINVAL, "output holds %lld bytes, need %lld", (long long)n, T);
+    if (!p->packed) return fail(TDG_ESTATE, "kernel mask before tdgemm_quantize_pack");
+    CU_TRY(cudaStreamSynchronize(p->last_stream));
+    CU_TRY(cudaMemcpy(out, p->kmask, (size_t)T, cudaMemcpyDeviceToHost));
+    return TDG_OK;
+}
+
 static PlanParams params_of(const tdgemm_plan_s *p) {
     PlanParams pp;
     pp.mode = p->mode; pp.form = p->form; pp.dtype = p->dtype;
@@ -366,6 +421,19 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
     const double *stab = p->have_table ? p->stab : nullptr;
     CU_TRY(launch_planner<T>(pp, p->mA, p->eA, p->mB, p->eB, stab, p->dplan, (T *)p->cA,
                              p->sA, (T *)p->cB, p->sB, (T *)p->pair, st));
+    if (p->kctrl_mode) {
+        CU_TRY(launch_kernel_control(pp, p->mA, p->eA, p->mB, p->eB, p->dplan, p->kctrl_mode,
+                                     p->kctrl_thr, p->kctrl_k, p->kratio, p->kmask, st));
+        OpShape s0 = op_shape(p, 0);
+        const bool directA = !nA && (p->lda * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)A & 15) == 0;
+        const bool directB = nB && (p->ldb * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)B & 15) == 0;
+        if (!directA)
+            CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, nullptr), 1, p->dplan, 0, 0, (T *)p->kA,
+                                    s0.a_ld, s0.a_rows, st));
+        if (!directB)
+            CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, nullptr), 1, p->dplan, 0, 0, (T *)p->kB,
+                                    s0.b_ld, s0.b_rows, st));
+    }
     if (is_tc_form(p->form)) {
         if constexpr (sizeof(T) == 4) {
             const long long ldk = round_up(p->K, 128);
@@ -447,7 +515,7 @@ static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cu
         r = make_map(&mb, dt, sizeof(T), bbase, s.b_cols, s.b_rows, ldb_op, bxb, bk,
                      CU_TENSOR_MAP_SWIZZLE_NONE);
         if (r != TDG_OK) return r;
-        GemmArgs<T> g;
+        GemmArgs<T> g{};
         g.plan = p->dplan;
         g.M = p->M; g.N = p->N; g.K = p->K;
         g.Mrows = s.a_cols;
@@ -458,7 +526,44 @@ static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cu
         g.C = C; g.ldc = p->ldc;
         g.alpha = (T)alpha; g.beta = (T)beta; g.beta_zero = beta == 0.0;
         g.Rbar = (!plain && (p->flags & TDG_KEEP_PACKED)) ? (T *)p->Rbar : nullptr;
+        g.kmask = p->kctrl_mode ? p->kmask : nullptr;
+        g.kmask_sense = 1;
         CU_TRY(launch_packed_gemm<T>(gform, Wk, g, ma, mb, st));
+    }
+    if (p->kctrl_mode) {
+        // the inner kernels left unaccelerated: conventional product (Sec. 6)
+        OpShape s = op_shape(p, 0);
+        int bxa, bxb, bk;
+        packed_gemm_boxes(p->dtype, G_PLAIN, &bxa, &bxb, &bk);
+        const void *abase = p->kA, *bbase = p->kB;
+        long long lda_op = s.a_ld, ldb_op = s.b_ld;
+        const bool nA = p->tA == 'N', nB = p->tB == 'N';
+        if (!nA && (p->lda * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)p->A_user & 15) == 0) {
+            abase = p->A_user; lda_op = p->lda;
+        }
+        if (nB && (p->ldb * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)p->B_user & 15) == 0) {
+            bbase = p->B_user; ldb_op = p->ldb;
+        }
+        CUtensorMap ma, mb;
+        tdg_status r = make_map(&ma, dt, sizeof(T), abase, s.a_cols, s.a_rows, lda_op, bxa, bk,
+                                CU_TENSOR_MAP_SWIZZLE_NONE);
+        if (r != TDG_OK) return r;
+        r = make_map(&mb, dt, sizeof(T), bbase, s.b_cols, s.b_rows, ldb_op, bxb, bk,
+                     CU_TENSOR_MAP_SWIZZLE_NONE);
+        if (r != TDG_OK) return r;
+        GemmArgs<T> g{};
+        g.plan = p->dplan;
+        g.M = p->M; g.N = p->N; g.K = p->K;
+        g.Mrows = s.a_cols; g.Krows = s.a_rows;
+        g.L = p->L; g.P = p->L;
+        g.nM = p->nM; g.nK = p->nK; g.nN = p->nN;
+        g.pair = (const T *)p->pair;
+        g.C = C; g.ldc = p->ldc;
+        g.alpha = (T)alpha; g.beta = (T)beta; g.beta_zero = beta == 0.0;
+        g.Rbar = nullptr;
+        g.kmask = p->kmask;
+        g.kmask_sense = 0;
+        CU_TRY(launch_packed_gemm<T>(G_PLAIN, 1, g, ma, mb, st));
     }
     return TDG_OK;
 }
@@ -590,6 +695,10 @@ extern "C" tdg_status tdgemm_plan_destroy(tdgemm_plan_t p) {
     if (p->hA) cudaFree(p->hA);
     if (p->hB) cudaFree(p->hB);
     if (p->hC) cudaFree(p->hC);
+    if (p->kA) cudaFree(p->kA);
+    if (p->kB) cudaFree(p->kB);
+    if (p->kratio) cudaFree(p->kratio);
+    if (p->kmask) cudaFree(p->kmask);
     delete p;
     return TDG_OK;
 }

@@ -30,6 +30,7 @@ struct DevPlan {
     int status;        // tdg_status raised on the device (0 = ok)
     int nonfinite;     // set by the statistics kernel
     double pred_snr;   // model SNR (dB), NaN if not modelled
+    double s_rep;      // representation-noise RMSE the model used (0 if none)
     double S, T1, T2, T3;  // noise-model aggregates
 };
 

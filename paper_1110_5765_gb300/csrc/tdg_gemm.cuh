@@ -186,7 +186,13 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
     constexpr int RG = Cfg::RG, CG = Cfg::CG, NCACC = Cfg::NCACC;
     constexpr bool TMEMC = Cfg::TMEMC;
 
-    if (g.plan->W != W) return;   // the device planner chose another packing
+    // the device planner chose another packing (with Sec. 6 control the plain
+    // kernel serves the kernels left unaccelerated, whatever W was chosen)
+    if (!(FORM == G_PLAIN && g.kmask) && g.plan->W != W) return;
+    if (g.kmask) {
+        const long long i = (long long)blockIdx.y * BM / g.L, j = (long long)blockIdx.x * BN / g.L;
+        if ((g.kmask[i * g.nN + j] != 0) != (g.kmask_sense != 0)) return;
+    }
 
     extern __shared__ __align__(128) unsigned char smem[];
     T *sA = reinterpret_cast<T *>(smem);

@@ -34,7 +34,15 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
                            DevPlan *plan, T *cA, double *sA, T *cB, double *sB, T *pair,
                            cudaStream_t st);
 
-// Pack kernels run only when the device plan's W equals expectW; W is the
+// Sec. 6 inner-kernel control: per-kernel predicted S/N and the mask of
+// kernels that run packed (mode 1: S/N >= thr; mode 2: the k best).
+cudaError_t launch_kernel_control(const PlanParams &pp, const double *mA, const double *vA,
+                                  const double *mB, const double *vB, const DevPlan *plan,
+                                  int mode, double thr, long long k, double *ratio,
+                                  unsigned char *mask, cudaStream_t st);
+
+// Pack kernels run only when the device plan's W equals expectW (expectW = 0:
+// always); W is the
 // packing of the kernel itself; wsign < 0 packs with z, > 0 with z^-1;
 // rows_out bounds the rows written to the k-major output.
 template <typename T>
@@ -63,6 +71,8 @@ struct GemmArgs {
     T alpha, beta;
     int beta_zero;
     T *Rbar;                // nullable: keep packed slab results
+    const unsigned char *kmask;   // nullable: Sec. 6 mask per L x L inner kernel
+    int kmask_sense;        // run the CTA tiles whose kernel's mask equals this
 };
 
 // Returns cudaErrorNotSupported when no kernel exists for (T, form, W).

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) pack_k_xc_kernel(Src<T> S, int P, const D
                                                         int expectW, int wsign, T *out,
                                                         long long ldo, long long rows_out,
                                                         int vec_ok) {
-    if (plan->W != expectW) return;
+    if (expectW > 0 && plan->W != expectW) return;
     constexpr int VEC = VecT<T>::n;
     const T w = W > 1 ? pack_weight<T>(plan, wsign) : T(1);
     const bool compand = S.c != nullptr;
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) pack_k_kc_kernel(Src<T> S, int P, const D
                                                         int expectW, int wsign, T *out,
                                                         long long ldo, long long rows_out,
                                                         int vec_ok) {
-    if (plan->W != expectW) return;
+    if (expectW > 0 && plan->W != expectW) return;
     constexpr int VEC = VecT<T>::n;
     constexpr int NK = TILE * W;            // k values per tile row
     constexpr int PITCH = NK + 1;
@@ -219,7 +219,7 @@ template <typename T, int W>
 __global__ void __launch_bounds__(256) pack_x_kernel(Src<T> S, int P, const DevPlan *plan,
                                                      int expectW, int wsign, T *out,
                                                      long long ldo) {
-    if (plan->W != expectW) return;
+    if (expectW > 0 && plan->W != expectW) return;
     constexpr int NX = TILE * W;
     constexpr int PITCH = TILE + 1;
     __shared__ T s[NX * PITCH];

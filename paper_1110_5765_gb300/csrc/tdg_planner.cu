@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
     a.status = 0;
     a.level = -1;
     a.pred_snr = NAN;
+    a.s_rep = 0.0;
 
     if (pp.form == TDG_PLAIN) {
         a.W = 1; a.q = 0; a.gA = a.gB = 0; a.R = 0; a.Wef = 0;
@@ -152,7 +153,10 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
             if (tbest >= pp.t0 && tbest < pp.t0 + pp.nt)
                 s = stab[(pp.Wreq - 2) * pp.nt + (tbest - pp.t0)];
         }
-        if (s >= 0.0) a.pred_snr = snr_db(a.S, model_noise(a, L, g, g, s, pp.noise_rms));
+        if (s >= 0.0) {
+            a.pred_snr = snr_db(a.S, model_noise(a, L, g, g, s, pp.noise_rms));
+            a.s_rep = s;
+        }
     } else {  // MODE_TARGET, packed forms
         int t_lo = 0;
         while (r_level(t_lo) < L) ++t_lo;
@@ -208,6 +212,12 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
             c.Wef = w_ef(c.R, c.q, pp.p);
             c.level = t;
             c.pred_snr = snr_db(a.S, n);
+            {
+                double sc = 0.0;
+                if (!(c.W <= w_ef(c.R, c.q, pp.p)) && stab && t >= pp.t0 && t < pp.t0 + pp.nt)
+                    sc = stab[(c.W - 2) * pp.nt + (t - pp.t0)];
+                c.s_rep = sc > 0.0 ? sc : 0.0;
+            }
             if (!have_first) { first = c; have_first = true; }
             if (c.pred_snr >= pp.target_db) { a = c; chosen = true; }
         }
@@ -269,7 +279,76 @@ __global__ void pairs_kernel(PlanParams pp, const double *__restrict__ sA,
     }
 }
 
+// ---- Sec. 6: per inner kernel R_ij, predicted S_ij / N_ij with the call's
+// companders (sums in ascending l, operation order as in the oracle)
+__global__ void kernel_ratio_kernel(PlanParams pp, const double *__restrict__ mA,
+                                    const double *__restrict__ vA, const double *__restrict__ mB,
+                                    const double *__restrict__ vB, const DevPlan *__restrict__ plan,
+                                    double *ratio) {
+    const long long T = (long long)pp.nM * pp.nN;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const int i = (int)(t / pp.nN), j = (int)(t % pp.nN);
+    const DevPlan a = *plan;
+    if (a.W < 2) { ratio[t] = 0.0; return; }
+    const double L = (double)pp.L;
+    const double gA2 = __dmul_rn((double)a.gA, (double)a.gA), gB2 = __dmul_rn((double)a.gB, (double)a.gB);
+    const double s = a.s_rep;
+    double S = 0.0, N = 0.0;
+    for (int l = 0; l < pp.nK; ++l) {
+        const double va = vA[(long long)i * pp.nK + l], vb = vB[(long long)l * pp.nN + j];
+        const double ma = mA[(long long)i * pp.nK + l], mb = mB[(long long)l * pp.nN + j];
+        const double ma2 = __dmul_rn(ma, ma), mb2 = __dmul_rn(mb, mb);
+        S = __dadd_rn(S, __dmul_rn(__dmul_rn(L, va), vb));
+        double n = __dadd_rn(__ddiv_rn(__dmul_rn(__dmul_rn(L, va), mb2), __dmul_rn(12.0, gB2)),
+                             __ddiv_rn(__dmul_rn(__dmul_rn(L, vb), ma2), __dmul_rn(12.0, gA2)));
+        if (pp.noise_rms) {
+            n = __dadd_rn(n, __ddiv_rn(__dmul_rn(__dmul_rn(ma2, mb2), __ddiv_rn(L, 144.0)),
+                                       __dmul_rn(gA2, gB2)));
+            n = __dadd_rn(n, __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(9.0, va), vb), __dmul_rn(s, s)),
+                                       __dmul_rn(gA2, gB2)));
+        } else {
+            n = __dadd_rn(n, __ddiv_rn(__dmul_rn(__dmul_rn(ma2, mb2),
+                                                 __dadd_rn(__ddiv_rn(L, 144.0), __dmul_rn(s, s))),
+                                       __dmul_rn(gA2, gB2)));
+        }
+        N = __dadd_rn(N, n);
+    }
+    ratio[t] = N > 0.0 ? __ddiv_rn(S, N) : INFINITY;
+}
+
+// mode 1: ratio >= thr;  mode 2: rank (descending ratio, ties to the lower
+// index) below k.  A plan that fell back to W = 1 accelerates nothing.
+__global__ void kernel_mask_kernel(long long T, int mode, double thr, long long k,
+                                   const DevPlan *__restrict__ plan,
+                                   const double *__restrict__ ratio, unsigned char *mask) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    if (plan->W < 2) { mask[t] = 0; return; }
+    const double r = ratio[t];
+    if (mode == 1) { mask[t] = r >= thr ? 1 : 0; return; }
+    long long rank = 0;
+    for (long long u = 0; u < T; ++u) {
+        const double ru = ratio[u];
+        rank += (ru > r || (ru == r && u < t)) ? 1 : 0;
+    }
+    mask[t] = rank < k ? 1 : 0;
+}
+
 }  // namespace
+
+cudaError_t launch_kernel_control(const PlanParams &pp, const double *mA, const double *vA,
+                                  const double *mB, const double *vB, const DevPlan *plan,
+                                  int mode, double thr, long long k, double *ratio,
+                                  unsigned char *mask, cudaStream_t st) {
+    const long long T = (long long)pp.nM * pp.nN;
+    const int g = (int)((T + 255) / 256);
+    kernel_ratio_kernel<<<g, 256, 0, st>>>(pp, mA, vA, mB, vB, plan, ratio);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    kernel_mask_kernel<<<g, 256, 0, st>>>(T, mode, thr, k, plan, ratio, mask);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double *eA,

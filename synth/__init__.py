@@ -29,6 +29,7 @@ __all__ = [
     "iid",
     "int_uniform",
     "blockwise_range_uniform",
+    "blockwise_crest",
     "eigenface_pixels",
     "mlp_teacher",
     "mlp_inputs",
@@ -88,6 +89,23 @@ def blockwise_range_uniform(shape, seed: int, L: int, dtype=np.float64,
     x = g.uniform(-1.0, 1.0, size=shape)
     scale = np.repeat(np.repeat(me, L, axis=0), L, axis=1)[:rows, :cols]
     return _cast(x * scale, dtype)
+
+
+def blockwise_crest(shape, seed: int, L: int, dtype=np.float64, kmax: int = 11,
+                    emin: int = 1, emax: int = 4096) -> np.ndarray:
+    """Per L x L block: sign(u) |u|^k * e with u uniform on [-1, 1], an odd
+    exponent k drawn from {1, 3, ..., kmax} and an integer range e drawn from
+    {emin, ..., emax}.  Larger k gives a larger peak-to-RMS ratio, so blocks
+    differ in both scale and shape."""
+    g = rng(seed)
+    rows, cols = shape
+    nbr, nbc = -(-rows // L), -(-cols // L)
+    k = 2 * g.integers(0, (kmax - 1) // 2 + 1, size=(nbr, nbc)) + 1
+    me = g.integers(emin, emax + 1, size=(nbr, nbc)).astype(np.float64)
+    u = g.uniform(-1.0, 1.0, size=shape)
+    kk = np.repeat(np.repeat(k, L, axis=0), L, axis=1)[:rows, :cols]
+    scale = np.repeat(np.repeat(me, L, axis=0), L, axis=1)[:rows, :cols]
+    return _cast(np.sign(u) * np.abs(u) ** kk * scale, dtype)
 
 
 def eigenface_pixels(pixels: int, images: int, seed: int, dtype=np.float32) -> np.ndarray:

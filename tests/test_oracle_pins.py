@@ -415,3 +415,94 @@ def test_rms_scaled_rep_noise_tracks_peaky_sources(orc, kind):
     agu = orc.aggregates(orc.block_stats(U, L), orc.block_stats(U, L), L)
     assert abs(orc.model_snr_db(agu, 30, 30, 50.0, rms=True) -
                orc.model_snr_db(agu, 30, 30, 50.0, rms=False)) < 0.1
+
+
+# ------------------------------------------------------------------ Sec. 6 inner-kernel control
+@pytest.mark.parametrize("rms", [False, True])
+def test_kernel_ratio_of_one_kernel_is_the_model_snr(orc, rms):
+    """With a single L x L output block the inner kernel's S / N is the
+    whole-matrix noise model of eqs. 19-21 (pinned above)."""
+    L = 64
+    A = synth.blockwise_crest((L, 3 * L), 31, L, np.float64)
+    B = synth.blockwise_crest((3 * L, L), 32, L, np.float64)
+    stA, stB = orc.block_stats(A, L), orc.block_stats(B, L)
+    ag = orc.aggregates(stA, stB, L)
+    for gA, gB, s in ((100, 300, 0.0), (31, 31, 2.5)):
+        r = orc.kernel_ratios(stA, stB, L, gA, gB, s, rms)
+        want = 10.0 ** (orc.model_snr_db(ag, gA, gB, s, rms) / 10.0)
+        assert r.shape == (1, 1)
+        assert abs(r[0, 0] / want - 1.0) < 1e-12
+
+
+def test_kernel_ratios_index_the_right_blocks(orc):
+    """Kernel (i, j) uses row-block i of A and column-block j of B: each ratio
+    equals the model evaluated on those two sub-matrices alone."""
+    L = 32
+    A = synth.blockwise_crest((3 * L, 2 * L), 33, L, np.float64)
+    B = synth.blockwise_crest((2 * L, 4 * L), 34, L, np.float64)
+    r = orc.kernel_ratios(orc.block_stats(A, L), orc.block_stats(B, L), L, 50, 70, 1.0)
+    assert r.shape == (3, 4)
+    for i in range(3):
+        for j in range(4):
+            Ai, Bj = A[i * L:(i + 1) * L], B[:, j * L:(j + 1) * L]
+            ag = orc.aggregates(orc.block_stats(Ai, L), orc.block_stats(Bj, L), L)
+            want = 10.0 ** (orc.model_snr_db(ag, 50, 70, 1.0) / 10.0)
+            assert abs(r[i, j] / want - 1.0) < 1e-12, (i, j)
+    assert np.ptp(10 * np.log10(r)) > 1.0       # the kernels really differ
+
+
+def test_kernel_mask_rules(orc):
+    """'fraction': exactly ceil(F T) kernels, highest ratio first, equal ratios
+    to the lower row-major index; 'snr': ratio >= 10^(value / 10)."""
+    r = np.array([[5.0, 1.0, 5.0], [2.0, 5.0, 0.5]])
+    m = orc.kernel_mask(r, "fraction", 0.34)          # ceil(2.04) = 3
+    assert m.tolist() == [[True, False, True], [False, True, False]]
+    m = orc.kernel_mask(r, "fraction", 0.25)          # ceil(1.5) = 2 of the three 5s
+    assert m.tolist() == [[True, False, True], [False, False, False]]
+    assert not orc.kernel_mask(r, "fraction", 0.0).any()
+    assert orc.kernel_mask(r, "fraction", 1.0).all()
+    m = orc.kernel_mask(r, "snr", 10.0 * math.log10(2.0))
+    assert m.tolist() == [[True, False, True], [True, True, False]]
+
+
+def test_kernel_control_endpoints_and_monotone_noise(orc):
+    """F = 0 is the conventional product and F = 1 the uncontrolled packed
+    product, bit for bit; in between the measured noise grows with F (each
+    added kernel trades exact outputs for packed ones)."""
+    L = 64
+    A = synth.blockwise_crest((192, 256), 35, L, np.float64)
+    B = synth.blockwise_crest((256, 256), 36, L, np.float64)
+    kw = dict(L=L, W=2, dtype="f64", form="sym", bits=10)
+    ref = orc.exact_gemm(A, B)
+    full = orc.tdgemm(A, B, **kw)
+    assert full.plan.W <= full.plan.Wef
+    r0 = orc.tdgemm(A, B, kernel_control=("fraction", 0.0), **kw)
+    r1 = orc.tdgemm(A, B, kernel_control=("fraction", 1.0), **kw)
+    assert np.array_equal(r0.C.view(np.uint8), orc.gemm_plain(A, B, "f64").view(np.uint8))
+    assert np.array_equal(r1.C.view(np.uint8), full.C.view(np.uint8))
+    noise = [float(np.sum((orc.tdgemm(A, B, kernel_control=("fraction", F), **kw).C - ref) ** 2))
+             for F in (0.0, 0.25, 0.5, 0.75, 1.0)]
+    assert all(a < b for a, b in zip(noise, noise[1:]))
+
+
+@pytest.mark.parametrize("gen", ["range_uniform", "crest"])
+def test_kernel_snr_prediction_against_measurement(orc, gen):
+    """Per inner kernel, inside the headroom (s = 0): on uniform blocks (the
+    paper's test matrices) the measured SNR of each L x L output block is the
+    predicted one within 0.6 dB; on peaky blocks the model is conservative
+    (small values round with less than the uniform-error variance): measured
+    between the prediction - 0.3 dB and + 3 dB."""
+    L = 64
+    mk = synth.blockwise_range_uniform if gen == "range_uniform" else synth.blockwise_crest
+    A = mk((192, 256), 37, L, np.float64)
+    B = mk((256, 256), 38, L, np.float64)
+    ref = orc.exact_gemm(A, B)
+    full = orc.tdgemm(A, B, L=L, W=2, dtype="f64", form="sym", bits=10)
+    pred = 10 * np.log10(orc.kernel_ratios(orc.block_stats(A, L), orc.block_stats(B, L), L,
+                                           full.plan.gA, full.plan.gB, 0.0))
+    lo, hi = (-0.6, 0.6) if gen == "range_uniform" else (-0.3, 3.0)
+    for i in range(3):
+        for j in range(4):
+            blk = (slice(i * L, (i + 1) * L), slice(j * L, (j + 1) * L))
+            d = orc.snr_db(full.C[blk], ref[blk]) - pred[i, j]
+            assert lo < d < hi, (i, j, d)
