@@ -441,6 +441,12 @@ def profile_case(form: str, n: int):
                      bits=8 if form == "tc_int" else 0)
     elif form == "plain":
         p = tdg.Plan(n, n, n, L=L_BLOCK, W=1, dtype="f32", form="plain")
+    elif form.startswith("sym_kc"):
+        # Sec. 6 control: fraction F of inner kernels accelerated, from the
+        # name (sym_kc50 = half of them)
+        p = tdg.Plan(n, n, n, L=L_BLOCK, W=W_PACK, dtype="f32", form="sym",
+                     target_snr_db=TARGET_DB)
+        p.set_kernel_control("fraction", int(form[6:] or "50") / 100.0)
     else:
         p = tdg.Plan(n, n, n, L=L_BLOCK, W=W_PACK, dtype="f32", form=form,
                      target_snr_db=TARGET_DB)
@@ -584,7 +590,8 @@ def main():
     ap.add_argument("--no-forms", dest="forms", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-case", default=None,
-                    help="plain|sym|asym|tc_int|tc_fp8: run a small case three times for ncu")
+                    help="plain|sym|asym|tc_int|tc_fp8|sym_kc<percent>: run one plan three "
+                         "times for ncu")
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--sweep", default=None, metavar="OUT.json",
                     help="run the 4096^3 distortion sweep (168 runs) and write its records")

@@ -166,10 +166,13 @@ tdg_status tdgemm_set_manual(tdgemm_plan_t plan, int q, double c_a, double c_b);
  *            of highest predicted S_ij / N_ij (ties to the lower row-major
  *            index); value in [0, 1]
  *
- * Valid for the SYM form with a planned (fixed-bit or target) plan, at most
- * 16384 inner kernels, and L a multiple of the GEMM CTA tile (128 for fp32,
- * 64 for fp64).  A plan whose planner fell back to W = 1 accelerates nothing.
- * TDG_EINVAL otherwise.  Allocates the mask, ratio and plain-operand buffers
+ * Valid for the SYM form with a planned (fixed-bit or target) plan without
+ * TDG_KEEP_PACKED, at most 16384 inner kernels, and L a multiple of the GEMM
+ * CTA tile (128 for fp32, 64 for fp64); TDG_EINVAL otherwise.  A plan whose
+ * planner fell back to W = 1 accelerates nothing.  Both kinds of inner kernel
+ * run in one GEMM launch (each CTA tile lies inside one inner kernel).
+ * Changing the setting requires tdgemm_quantize_pack again (TDG_ESTATE from
+ * tdgemm_gemm otherwise).  Allocates the mask, ratio and plain-operand buffers
  * on the first call that turns control on; they are freed with the plan.
  */
 tdg_status tdgemm_set_kernel_control(tdgemm_plan_t plan, int mode, double value);

@@ -41,42 +41,14 @@ void tdg::record_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", m
                         __FILE__, __LINE__);                                          \
     } while (0)
 
-// ---------------------------------------------------------------------------
-// TMA descriptors through the driver entry point (no -lcuda needed)
-// ---------------------------------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
-    return fn;
-}
-
-// 2-D map over a row-major [rows][cols] array with leading dimension ld.
+// 2-D TMA map over a row-major [rows][cols] array with leading dimension ld.
 static tdg_status make_map(CUtensorMap *m, CUtensorMapDataType dt, size_t esz, const void *base,
                            long long cols, long long rows, long long ld, int box_cols,
                            int box_rows, CUtensorMapSwizzle sw) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return fail(TDG_ECUDA, "cuTensorMapEncodeTiled is not available");
-    if (((uintptr_t)base & 15) || ((ld * (long long)esz) & 15))
+    CUresult r = encode_map_2d(m, dt, esz, base, cols, rows, ld, box_cols, box_rows, sw);
+    if (r == CUDA_ERROR_NOT_SUPPORTED) return fail(TDG_ECUDA, "cuTensorMapEncodeTiled is not available");
+    if (r == CUDA_ERROR_INVALID_VALUE && (((uintptr_t)base & 15) || ((ld * (long long)esz) & 15)))
         return fail(TDG_EINVAL, "TMA operand not 16-byte aligned (ld=%lld)", ld);
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * (long long)esz)};
-    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(TDG_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return TDG_OK;
 }
@@ -136,8 +108,7 @@ static std::vector<int> candidates(const tdgemm_plan_s *p) {
     if (p->form == TDG_PLAIN || is_tc_form(p->form)) return {1};
     if (p->mode == MODE_TARGET) {
         for (int w = p->W; w >= 2; --w) c.push_back(w);
-        // 0: plain fallback (with Sec. 6 control the masked plain launch covers it)
-        if ((p->flags & TDG_ALLOW_FALLBACK) && !p->kctrl_mode) c.push_back(0);
+        if (p->flags & TDG_ALLOW_FALLBACK) c.push_back(0);   // 0: plain fallback
     } else {
         c.push_back(p->W);
     }
@@ -326,15 +297,21 @@ extern "C" tdg_status tdgemm_set_kernel_control(tdgemm_plan_t p, int mode, doubl
     if (p->form != TDG_SYM) return fail(TDG_EINVAL, "inner-kernel control needs the SYM form");
     if (p->mode == MODE_MANUAL) return fail(TDG_EINVAL, "inner-kernel control needs a planned (not manual) plan");
     if (mode != 1 && mode != 2) return fail(TDG_EINVAL, "mode must be 0, 1 (SNR) or 2 (fraction)");
+    if (p->flags & TDG_KEEP_PACKED)
+        return fail(TDG_EINVAL, "inner-kernel control does not keep packed slab results");
     if (!isfinite(value)) return fail(TDG_EINVAL, "value must be finite");
     if (mode == 2 && (value < 0.0 || value > 1.0)) return fail(TDG_EINVAL, "fraction must be in [0, 1]");
-    for (int gf : {G_SYM, G_PLAIN}) {
-        int bxa, bxb, bk;
-        packed_gemm_boxes(p->dtype, gf, &bxa, &bxb, &bk);
-        if (p->L % bxa || p->L % bxb)
+    {
+        // the mixed launch runs both kinds of tile with one box shape
+        int sa, sb, sk, pa, pb, pk;
+        packed_gemm_boxes(p->dtype, G_SYM, &sa, &sb, &sk);
+        packed_gemm_boxes(p->dtype, G_PLAIN, &pa, &pb, &pk);
+        if (sa != pa || sb != pb || sk != pk)
+            return fail(TDG_EUNSUPPORTED, "packed and plain tiles differ for this dtype");
+        if (p->L % sa || p->L % sb)
             return fail(TDG_EINVAL,
                         "inner-kernel control needs L to be a multiple of the %dx%d CTA tile",
-                        bxa, bxb);
+                        sa, sb);
     }
     const long long T = (long long)p->nM * p->nN;
     if (T > 16384) return fail(TDG_EINVAL, "inner-kernel control supports up to 16384 inner kernels");
@@ -488,33 +465,31 @@ extern "C" tdg_status tdgemm_quantize_pack(tdgemm_plan_t p, const void *A, const
 
 template <typename T>
 static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cudaStream_t st) {
-    const CUtensorMapDataType dt =
-        sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    // the plain k-major operands: the caller's buffers where their layout and
+    // alignment already fit, else the copies the pack step made
+    auto plain_ops = [&](const void *abuf, const void *bbuf, GemmOperand &a, GemmOperand &b) {
+        OpShape s = op_shape(p, 0);
+        a = {abuf, s.a_cols, s.a_rows, s.a_ld};
+        b = {bbuf, s.b_cols, s.b_rows, s.b_ld};
+        if (p->tA != 'N' && (p->lda * (long long)sizeof(T)) % 16 == 0 &&
+            ((uintptr_t)p->A_user & 15) == 0)
+            a = {p->A_user, s.a_cols, s.a_rows, p->lda};
+        if (p->tB == 'N' && (p->ldb * (long long)sizeof(T)) % 16 == 0 &&
+            ((uintptr_t)p->B_user & 15) == 0)
+            b = {p->B_user, s.b_cols, s.b_rows, p->ldb};
+    };
     for (int w : candidates(p)) {
         const bool plain = (w == 0 || p->form == TDG_PLAIN);
         const int gform = plain ? G_PLAIN : (p->form == TDG_SYM ? G_SYM : G_ASYM);
         const int Wk = plain ? 1 : w;
         OpShape s = op_shape(p, w);
-        int bxa, bxb, bk;
-        packed_gemm_boxes(p->dtype, gform, &bxa, &bxb, &bk);
-        const void *abase = p->Abuf, *bbase = p->Bbuf;
-        long long lda_op = s.a_ld, ldb_op = s.b_ld;
+        GemmOperands ops{};
         if (plain) {
-            const bool nA = p->tA == 'N', nB = p->tB == 'N';
-            if (!nA && (p->lda * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)p->A_user & 15) == 0) {
-                abase = p->A_user; lda_op = p->lda;
-            }
-            if (nB && (p->ldb * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)p->B_user & 15) == 0) {
-                bbase = p->B_user; ldb_op = p->ldb;
-            }
+            plain_ops(p->Abuf, p->Bbuf, ops.a, ops.b);
+        } else {
+            ops.a = {p->Abuf, s.a_cols, s.a_rows, s.a_ld};
+            ops.b = {p->Bbuf, s.b_cols, s.b_rows, s.b_ld};
         }
-        CUtensorMap ma, mb;
-        tdg_status r = make_map(&ma, dt, sizeof(T), abase, s.a_cols, s.a_rows, lda_op, bxa, bk,
-                                CU_TENSOR_MAP_SWIZZLE_NONE);
-        if (r != TDG_OK) return r;
-        r = make_map(&mb, dt, sizeof(T), bbase, s.b_cols, s.b_rows, ldb_op, bxb, bk,
-                     CU_TENSOR_MAP_SWIZZLE_NONE);
-        if (r != TDG_OK) return r;
         GemmArgs<T> g{};
         g.plan = p->dplan;
         g.M = p->M; g.N = p->N; g.K = p->K;
@@ -526,44 +501,17 @@ static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cu
         g.C = C; g.ldc = p->ldc;
         g.alpha = (T)alpha; g.beta = (T)beta; g.beta_zero = beta == 0.0;
         g.Rbar = (!plain && (p->flags & TDG_KEEP_PACKED)) ? (T *)p->Rbar : nullptr;
-        g.kmask = p->kctrl_mode ? p->kmask : nullptr;
-        g.kmask_sense = 1;
-        CU_TRY(launch_packed_gemm<T>(gform, Wk, g, ma, mb, st));
-    }
-    if (p->kctrl_mode) {
-        // the inner kernels left unaccelerated: conventional product (Sec. 6)
-        OpShape s = op_shape(p, 0);
-        int bxa, bxb, bk;
-        packed_gemm_boxes(p->dtype, G_PLAIN, &bxa, &bxb, &bk);
-        const void *abase = p->kA, *bbase = p->kB;
-        long long lda_op = s.a_ld, ldb_op = s.b_ld;
-        const bool nA = p->tA == 'N', nB = p->tB == 'N';
-        if (!nA && (p->lda * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)p->A_user & 15) == 0) {
-            abase = p->A_user; lda_op = p->lda;
+        if (p->kctrl_mode && !plain) {
+            // Sec. 6: the tiles of inner kernels left unaccelerated compute the
+            // conventional product from the plain operands, same launch
+            plain_ops(p->kA, p->kB, ops.pa, ops.pb);
+            g.kmask = p->kmask;
         }
-        if (nB && (p->ldb * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)p->B_user & 15) == 0) {
-            bbase = p->B_user; ldb_op = p->ldb;
-        }
-        CUtensorMap ma, mb;
-        tdg_status r = make_map(&ma, dt, sizeof(T), abase, s.a_cols, s.a_rows, lda_op, bxa, bk,
-                                CU_TENSOR_MAP_SWIZZLE_NONE);
-        if (r != TDG_OK) return r;
-        r = make_map(&mb, dt, sizeof(T), bbase, s.b_cols, s.b_rows, ldb_op, bxb, bk,
-                     CU_TENSOR_MAP_SWIZZLE_NONE);
-        if (r != TDG_OK) return r;
-        GemmArgs<T> g{};
-        g.plan = p->dplan;
-        g.M = p->M; g.N = p->N; g.K = p->K;
-        g.Mrows = s.a_cols; g.Krows = s.a_rows;
-        g.L = p->L; g.P = p->L;
-        g.nM = p->nM; g.nK = p->nK; g.nN = p->nN;
-        g.pair = (const T *)p->pair;
-        g.C = C; g.ldc = p->ldc;
-        g.alpha = (T)alpha; g.beta = (T)beta; g.beta_zero = beta == 0.0;
-        g.Rbar = nullptr;
-        g.kmask = p->kmask;
-        g.kmask_sense = 0;
-        CU_TRY(launch_packed_gemm<T>(G_PLAIN, 1, g, ma, mb, st));
+        cudaError_t e = launch_packed_gemm<T>(gform, Wk, g, ops, st);
+        if (e == cudaErrorInvalidValue)
+            return fail(TDG_ECUDA, "packed GEMM: an operand could not be mapped for TMA");
+        if (e != cudaSuccess)
+            return fail(TDG_ECUDA, "packed GEMM launch failed: %s", cudaGetErrorString(e));
     }
     return TDG_OK;
 }

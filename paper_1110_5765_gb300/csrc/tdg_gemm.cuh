@@ -176,23 +176,34 @@ struct SlabWalk {
     }
 };
 
+// MIX (symmetric form, Sec. 6 control): each CTA tile reads its inner
+// kernel's mask; where it is 0 the tile runs the conventional product (one fma
+// chain over all of K from the plain operands, no slab epilogue) instead of
+// the packed one.  Tiles never straddle inner kernels (L is a multiple of the
+// tile), and the block scheduler balances the two kinds of tile.
 template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES,
-          bool KEEP>
+          bool KEEP, bool MIX>
 __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>::NT,
                                   GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>::MIN_CTAS)
     packed_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
-                       const __grid_constant__ CUtensorMap mapB, const GemmArgs<T> g) {
+                       const __grid_constant__ CUtensorMap mapB,
+                       const __grid_constant__ CUtensorMap mapPA,
+                       const __grid_constant__ CUtensorMap mapPB, const GemmArgs<T> g) {
     using Cfg = GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>;
     constexpr int RG = Cfg::RG, CG = Cfg::CG, NCACC = Cfg::NCACC;
     constexpr bool TMEMC = Cfg::TMEMC;
+    static_assert(!MIX || (FORM == G_SYM && !KEEP), "mixed tiles: symmetric form only");
 
-    // the device planner chose another packing (with Sec. 6 control the plain
-    // kernel serves the kernels left unaccelerated, whatever W was chosen)
-    if (!(FORM == G_PLAIN && g.kmask) && g.plan->W != W) return;
-    if (g.kmask) {
-        const long long i = (long long)blockIdx.y * BM / g.L, j = (long long)blockIdx.x * BN / g.L;
-        if ((g.kmask[i * g.nN + j] != 0) != (g.kmask_sense != 0)) return;
-    }
+    // the device planner chose another packing
+    if (g.plan->W != W) return;
+    // this CTA's tile, row-major over ntn tiles per row
+    const long long tmi = (long long)(blockIdx.x / g.ntn);
+    const long long x0 = tmi * BM;                      // first A-operand column (m or packed row)
+    const long long n0 = ((long long)blockIdx.x - tmi * g.ntn) * BN;
+    bool plain_tile = false;
+    if constexpr (MIX) plain_tile = g.kmask[(x0 / g.L) * g.nN + n0 / g.L] == 0;
+    const CUtensorMap *mA = plain_tile ? &mapPA : &mapA;
+    const CUtensorMap *mB = plain_tile ? &mapPB : &mapB;
 
     extern __shared__ __align__(128) unsigned char smem[];
     T *sA = reinterpret_cast<T *>(smem);
@@ -202,10 +213,11 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    const long long x0 = (long long)blockIdx.y * BM;   // first A-operand column (m or packed row)
-    const long long n0 = (long long)blockIdx.x * BN;
     const SlabWalk<T, FORM> walk{g};
-    const int nslab = walk.nslab();
+    const SlabWalk<T, G_PLAIN> pwalk{g};
+    const int nslab = plain_tile ? 1 : walk.nslab();
+    auto slab_len = [&](int l) { return plain_tile ? pwalk.len(l) : walk.len(l); };
+    auto slab_row0 = [&](int l) { return plain_tile ? 0LL : walk.row0(l); };
 
     // ---- loads: thread 0 keeps STAGES - 1 tiles in flight ahead of the math
     int pl = 0, ps = 0, issued = 0;    // next tile to load: slab pl, stage ps
@@ -213,18 +225,18 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         if (pl >= nslab) return;
         const int stage = issued % STAGES;
         mbar_arrive_expect_tx(&full[stage], (uint32_t)(Cfg::STAGE_A + Cfg::STAGE_B));
-        const int y = (int)(walk.row0(pl) + (long long)ps * BK);
-        tma_load_2d(sA + (size_t)stage * BK * BM, &mapA, &full[stage], (int)x0, y);
-        tma_load_2d(sB + (size_t)stage * BK * BN, &mapB, &full[stage], (int)n0, y);
+        const int y = (int)(slab_row0(pl) + (long long)ps * BK);
+        tma_load_2d(sA + (size_t)stage * BK * BM, mA, &full[stage], (int)x0, y);
+        tma_load_2d(sB + (size_t)stage * BK * BN, mB, &full[stage], (int)n0, y);
         ++issued;
-        if ((++ps) * BK >= walk.len(pl)) { ps = 0; ++pl; }
+        if ((++ps) * BK >= slab_len(pl)) { ps = 0; ++pl; }
     };
     if (TMEMC && warp == 0) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
         fence_barrier_init();
-        tma_prefetch_desc(&mapA);
-        tma_prefetch_desc(&mapB);
+        tma_prefetch_desc(mA);
+        tma_prefetch_desc(mB);
         for (int s = 0; s < STAGES; ++s) issue_next();
     }
     if (TMEMC) tmem_fence_before();
@@ -298,7 +310,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
     int it = 0;
     bool ok = true;
     for (int l = 0; l < nslab && ok; ++l) {
-        const int slen = walk.len(l);
+        const int slen = slab_len(l);
         for (int s = 0; s * BK < slen; ++s, ++it) {
             const int stage = it % STAGES;
             const bool got = mbar_wait_bounded(&full[stage], (it / STAGES) & 1);
@@ -344,7 +356,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
             }
         }
         if (!ok) break;
-        if (FORM == G_PLAIN) continue;
+        if (FORM == G_PLAIN || plain_tile) continue;
 
         // ---- slab end: keep (optionally), unpack, de-compand, accumulate.
         // The unpacked values stream through in the order f = e * NCACC + d
@@ -412,6 +424,15 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         // let every copy this CTA issued land before it exits
         if (tid == 0)
             for (int k = it; k < issued; ++k) mbar_wait_bounded(&full[k % STAGES], (k / STAGES) & 1);
+    } else if (MIX && plain_tile) {
+        // ------------------------------------------------------------ store C
+        // of a conventional-product tile, straight from the fma chains
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const long long row = out_row(i, 0);
+#pragma unroll
+            for (int j = 0; j < TN; ++j) store_c(row, out_col(j), acc[i][j]);
+        }
     } else if constexpr (TMEMC) {
         // ------------------------------------------------------------ store C
         // from the running sums in TMEM, 16 columns at a time (kept out of
@@ -448,12 +469,11 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
     }
 }
 
-template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES,
-          bool KEEP>
-cudaError_t launch_keep(const GemmArgs<T> &g, const CUtensorMap &mapA, const CUtensorMap &mapB,
-                        cudaStream_t st) {
-    using Cfg = GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>;
-    auto kern = packed_gemm_kernel<T, FORM, W, BM, BN, TM, TN, BK, STAGES, KEEP>;
+// One launch over the whole tile grid of shape C.
+template <typename T, int FORM, int W, typename C, bool KEEP, bool MIX>
+cudaError_t launch_grid(const GemmArgs<T> &g0, const GemmOperands &ops, cudaStream_t st) {
+    using Cfg = GemmCfg<T, FORM, W, C::BM, C::BN, C::TM, C::TN, C::BK, C::STAGES>;
+    auto kern = packed_gemm_kernel<T, FORM, W, C::BM, C::BN, C::TM, C::TN, C::BK, C::STAGES, KEEP, MIX>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
@@ -461,19 +481,42 @@ cudaError_t launch_keep(const GemmArgs<T> &g, const CUtensorMap &mapA, const CUt
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.Mrows + BM - 1) / BM));
-    kern<<<grid, Cfg::NT, Cfg::SMEM, st>>>(mapA, mapB, g);
+    const CUtensorMapDataType dt =
+        sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    auto map = [&](CUtensorMap *m, const GemmOperand &o, int box) {
+        return encode_map_2d(m, dt, sizeof(T), o.base, o.cols, o.rows, o.ld, box, C::BK,
+                             CU_TENSOR_MAP_SWIZZLE_NONE) == CUDA_SUCCESS;
+    };
+    CUtensorMap ma, mb, mpa, mpb;
+    if (!map(&ma, ops.a, C::BM) || !map(&mb, ops.b, C::BN)) return cudaErrorInvalidValue;
+    if (MIX) {
+        if (!map(&mpa, ops.pa, C::BM) || !map(&mpb, ops.pb, C::BN)) return cudaErrorInvalidValue;
+    } else {
+        mpa = ma;
+        mpb = mb;
+    }
+    GemmArgs<T> g = g0;
+    g.ntn = (int)((g.N + C::BN - 1) / C::BN);
+    const long long ntiles = ((g.Mrows + C::BM - 1) / C::BM) * g.ntn;
+    if (ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    kern<<<(unsigned)ntiles, Cfg::NT, Cfg::SMEM, st>>>(ma, mb, mpa, mpb, g);
     return cudaGetLastError();
 }
 
-// KEEP (store every packed slab result for tdgemm_unpack) is a separate
-// instantiation so the usual kernel carries none of that code.
-template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES>
-cudaError_t launch_cfg(const GemmArgs<T> &g, const CUtensorMap &mapA, const CUtensorMap &mapB,
-                       cudaStream_t st) {
-    if (FORM != G_PLAIN && g.Rbar)
-        return launch_keep<T, FORM, W, BM, BN, TM, TN, BK, STAGES, true>(g, mapA, mapB, st);
-    return launch_keep<T, FORM, W, BM, BN, TM, TN, BK, STAGES, false>(g, mapA, mapB, st);
+// KEEP (store every packed slab result for tdgemm_unpack) and MIX (Sec. 6
+// mixed tiles) are separate instantiations so the usual kernel carries none of
+// that code.
+template <typename T, int FORM, int W, typename C>
+cudaError_t launch_cfg(const GemmArgs<T> &g, const GemmOperands &ops, cudaStream_t st) {
+    if constexpr (FORM == G_SYM) {
+        if (g.kmask) {
+            if (g.Rbar || !ops.pa.base || !ops.pb.base) return cudaErrorInvalidValue;
+            return launch_grid<T, FORM, W, C, false, true>(g, ops, st);
+        }
+    }
+    if (g.kmask) return cudaErrorInvalidValue;
+    if (FORM != G_PLAIN && g.Rbar) return launch_grid<T, FORM, W, C, true, false>(g, ops, st);
+    return launch_grid<T, FORM, W, C, false, false>(g, ops, st);
 }
 
 }  // namespace tdg

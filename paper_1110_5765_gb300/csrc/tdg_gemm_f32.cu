@@ -5,32 +5,30 @@
 namespace tdg {
 
 template <int FORM, int W, typename C>
-static cudaError_t go(const GemmArgs<float> &g, const CUtensorMap &a, const CUtensorMap &b,
-                      cudaStream_t st) {
-    return launch_cfg<float, FORM, W, C::BM, C::BN, C::TM, C::TN, C::BK, C::STAGES>(g, a, b, st);
+static cudaError_t go(const GemmArgs<float> &g, const GemmOperands &ops, cudaStream_t st) {
+    return launch_cfg<float, FORM, W, C>(g, ops, st);
 }
 
 template <>
 cudaError_t launch_packed_gemm<float>(int form, int W, const GemmArgs<float> &g,
-                                      const CUtensorMap &mapA, const CUtensorMap &mapB,
-                                      cudaStream_t st) {
+                                      const GemmOperands &ops, cudaStream_t st) {
     using S = TilesF32;
     using A = TilesF32Asym;
-    if (form == G_PLAIN) return go<G_PLAIN, 1, S>(g, mapA, mapB, st);
+    if (form == G_PLAIN) return go<G_PLAIN, 1, S>(g, ops, st);
     if (form == G_SYM) {
         switch (W) {
-            case 1: return go<G_SYM, 1, S>(g, mapA, mapB, st);
-            case 2: return go<G_SYM, 2, S>(g, mapA, mapB, st);
-            case 3: return go<G_SYM, 3, S>(g, mapA, mapB, st);
-            case 4: return go<G_SYM, 4, S>(g, mapA, mapB, st);
+            case 1: return go<G_SYM, 1, S>(g, ops, st);
+            case 2: return go<G_SYM, 2, S>(g, ops, st);
+            case 3: return go<G_SYM, 3, S>(g, ops, st);
+            case 4: return go<G_SYM, 4, S>(g, ops, st);
         }
     }
     if (form == G_ASYM) {
         switch (W) {
-            case 1: return go<G_ASYM, 1, A>(g, mapA, mapB, st);
-            case 2: return go<G_ASYM, 2, A>(g, mapA, mapB, st);
-            case 3: return go<G_ASYM, 3, A>(g, mapA, mapB, st);
-            case 4: return go<G_ASYM, 4, A>(g, mapA, mapB, st);
+            case 1: return go<G_ASYM, 1, A>(g, ops, st);
+            case 2: return go<G_ASYM, 2, A>(g, ops, st);
+            case 3: return go<G_ASYM, 3, A>(g, ops, st);
+            case 4: return go<G_ASYM, 4, A>(g, ops, st);
         }
     }
     return cudaErrorNotSupported;

@@ -6,31 +6,29 @@
 namespace tdg {
 
 template <int FORM, int W, typename C>
-static cudaError_t go(const GemmArgs<double> &g, const CUtensorMap &a, const CUtensorMap &b,
-                      cudaStream_t st) {
-    return launch_cfg<double, FORM, W, C::BM, C::BN, C::TM, C::TN, C::BK, C::STAGES>(g, a, b, st);
+static cudaError_t go(const GemmArgs<double> &g, const GemmOperands &ops, cudaStream_t st) {
+    return launch_cfg<double, FORM, W, C>(g, ops, st);
 }
 
 template <>
 cudaError_t launch_packed_gemm<double>(int form, int W, const GemmArgs<double> &g,
-                                       const CUtensorMap &mapA, const CUtensorMap &mapB,
-                                       cudaStream_t st) {
+                                       const GemmOperands &ops, cudaStream_t st) {
     using D = TilesF64;
-    if (form == G_PLAIN) return go<G_PLAIN, 1, D>(g, mapA, mapB, st);
+    if (form == G_PLAIN) return go<G_PLAIN, 1, D>(g, ops, st);
     if (form == G_SYM) {
         switch (W) {
-            case 1: return go<G_SYM, 1, D>(g, mapA, mapB, st);
-            case 2: return go<G_SYM, 2, D>(g, mapA, mapB, st);
-            case 3: return go<G_SYM, 3, D>(g, mapA, mapB, st);
-            case 4: return go<G_SYM, 4, D>(g, mapA, mapB, st);
+            case 1: return go<G_SYM, 1, D>(g, ops, st);
+            case 2: return go<G_SYM, 2, D>(g, ops, st);
+            case 3: return go<G_SYM, 3, D>(g, ops, st);
+            case 4: return go<G_SYM, 4, D>(g, ops, st);
         }
     }
     if (form == G_ASYM) {
         switch (W) {
-            case 1: return go<G_ASYM, 1, D>(g, mapA, mapB, st);
-            case 2: return go<G_ASYM, 2, D>(g, mapA, mapB, st);
-            case 3: return go<G_ASYM, 3, D>(g, mapA, mapB, st);
-            case 4: return go<G_ASYM, 4, D>(g, mapA, mapB, st);
+            case 1: return go<G_ASYM, 1, D>(g, ops, st);
+            case 2: return go<G_ASYM, 2, D>(g, ops, st);
+            case 3: return go<G_ASYM, 3, D>(g, ops, st);
+            case 4: return go<G_ASYM, 4, D>(g, ops, st);
         }
     }
     return cudaErrorNotSupported;

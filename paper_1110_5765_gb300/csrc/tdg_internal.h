@@ -71,14 +71,37 @@ struct GemmArgs {
     T alpha, beta;
     int beta_zero;
     T *Rbar;                // nullable: keep packed slab results
-    const unsigned char *kmask;   // nullable: Sec. 6 mask per L x L inner kernel
-    int kmask_sense;        // run the CTA tiles whose kernel's mask equals this
+    // nullable: Sec. 6 mask per L x L inner kernel (symmetric form only).  A
+    // CTA tile whose kernel's mask is 0 computes the conventional product from
+    // the plain operands in the same launch.
+    const unsigned char *kmask;
+    int ntn;                // set by the launcher: tiles per row of the 1-D tile grid
 };
 
-// Returns cudaErrorNotSupported when no kernel exists for (T, form, W).
+// 2-D TMA map over a row-major [rows][cols] array with leading dimension ld
+// (elements), box {box_cols, box_rows}.  CUDA_ERROR_NOT_SUPPORTED when the
+// driver entry point is missing, CUDA_ERROR_INVALID_VALUE when the base or
+// the row pitch is not 16-byte aligned.
+CUresult encode_map_2d(CUtensorMap *m, CUtensorMapDataType dt, size_t esz, const void *base,
+                       long long cols, long long rows, long long ld, int box_cols, int box_rows,
+                       CUtensorMapSwizzle sw);
+
+// A k-major operand of the CUDA-core GEMM: [rows = k][cols = x], pitch ld.
+struct GemmOperand {
+    const void *base;
+    long long cols, rows, ld;
+};
+struct GemmOperands {
+    GemmOperand a, b;       // the operands of the launch's form
+    GemmOperand pa, pb;     // plain op(A)^T and op(B) for mixed tiles (g.kmask)
+};
+
+// Builds the tensor maps for its tile shape and launches.  Returns cudaErrorNotSupported when no
+// kernel exists for (T, form, W), cudaErrorInvalidValue when an operand
+// cannot be mapped.
 template <typename T>
-cudaError_t launch_packed_gemm(int form, int W, const GemmArgs<T> &g, const CUtensorMap &mapA,
-                               const CUtensorMap &mapB, cudaStream_t st);
+cudaError_t launch_packed_gemm(int form, int W, const GemmArgs<T> &g, const GemmOperands &ops,
+                               cudaStream_t st);
 
 // Tile shape the packed GEMM uses for (T, form): operand boxes are
 // {box_x_a, bk} for A and {box_x_b, bk} for B.

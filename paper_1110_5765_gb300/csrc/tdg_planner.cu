@@ -280,59 +280,95 @@ __global__ void pairs_kernel(PlanParams pp, const double *__restrict__ sA,
 }
 
 // ---- Sec. 6: per inner kernel R_ij, predicted S_ij / N_ij with the call's
-// companders (sums in ascending l, operation order as in the oracle)
+// companders.  One warp per inner kernel: lane u computes the terms of slab
+// l0 + u, then every lane adds them in ascending l (the oracle's order), so
+// the FP64 divisions spread over the warp while the sums keep their order.
+__device__ inline void kernel_terms(const PlanParams &pp, const DevPlan &a, double va,
+                                    double vb, double ma, double mb, double &s_out,
+                                    double &n_out) {
+    const double L = (double)pp.L;
+    const double gA2 = __dmul_rn((double)a.gA, (double)a.gA), gB2 = __dmul_rn((double)a.gB, (double)a.gB);
+    const double s = a.s_rep;
+    const double ma2 = __dmul_rn(ma, ma), mb2 = __dmul_rn(mb, mb);
+    s_out = __dmul_rn(__dmul_rn(L, va), vb);
+    double n = __dadd_rn(__ddiv_rn(__dmul_rn(__dmul_rn(L, va), mb2), __dmul_rn(12.0, gB2)),
+                         __ddiv_rn(__dmul_rn(__dmul_rn(L, vb), ma2), __dmul_rn(12.0, gA2)));
+    if (pp.noise_rms) {
+        n = __dadd_rn(n, __ddiv_rn(__dmul_rn(__dmul_rn(ma2, mb2), __ddiv_rn(L, 144.0)),
+                                   __dmul_rn(gA2, gB2)));
+        n = __dadd_rn(n, __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(9.0, va), vb), __dmul_rn(s, s)),
+                                   __dmul_rn(gA2, gB2)));
+    } else {
+        n = __dadd_rn(n, __ddiv_rn(__dmul_rn(__dmul_rn(ma2, mb2),
+                                             __dadd_rn(__ddiv_rn(L, 144.0), __dmul_rn(s, s))),
+                                   __dmul_rn(gA2, gB2)));
+    }
+    n_out = n;
+}
+
 __global__ void kernel_ratio_kernel(PlanParams pp, const double *__restrict__ mA,
                                     const double *__restrict__ vA, const double *__restrict__ mB,
                                     const double *__restrict__ vB, const DevPlan *__restrict__ plan,
                                     double *ratio) {
     const long long T = (long long)pp.nM * pp.nN;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
+    const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= T) return;                      // uniform per warp
     const int i = (int)(t / pp.nN), j = (int)(t % pp.nN);
     const DevPlan a = *plan;
-    if (a.W < 2) { ratio[t] = 0.0; return; }
-    const double L = (double)pp.L;
-    const double gA2 = __dmul_rn((double)a.gA, (double)a.gA), gB2 = __dmul_rn((double)a.gB, (double)a.gB);
-    const double s = a.s_rep;
-    double S = 0.0, N = 0.0;
-    for (int l = 0; l < pp.nK; ++l) {
-        const double va = vA[(long long)i * pp.nK + l], vb = vB[(long long)l * pp.nN + j];
-        const double ma = mA[(long long)i * pp.nK + l], mb = mB[(long long)l * pp.nN + j];
-        const double ma2 = __dmul_rn(ma, ma), mb2 = __dmul_rn(mb, mb);
-        S = __dadd_rn(S, __dmul_rn(__dmul_rn(L, va), vb));
-        double n = __dadd_rn(__ddiv_rn(__dmul_rn(__dmul_rn(L, va), mb2), __dmul_rn(12.0, gB2)),
-                             __ddiv_rn(__dmul_rn(__dmul_rn(L, vb), ma2), __dmul_rn(12.0, gA2)));
-        if (pp.noise_rms) {
-            n = __dadd_rn(n, __ddiv_rn(__dmul_rn(__dmul_rn(ma2, mb2), __ddiv_rn(L, 144.0)),
-                                       __dmul_rn(gA2, gB2)));
-            n = __dadd_rn(n, __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(9.0, va), vb), __dmul_rn(s, s)),
-                                       __dmul_rn(gA2, gB2)));
-        } else {
-            n = __dadd_rn(n, __ddiv_rn(__dmul_rn(__dmul_rn(ma2, mb2),
-                                                 __dadd_rn(__ddiv_rn(L, 144.0), __dmul_rn(s, s))),
-                                       __dmul_rn(gA2, gB2)));
-        }
-        N = __dadd_rn(N, n);
+    if (a.W < 2) {
+        if (lane == 0) ratio[t] = 0.0;
+        return;
     }
-    ratio[t] = N > 0.0 ? __ddiv_rn(S, N) : INFINITY;
+    double S = 0.0, N = 0.0;
+    for (int l0 = 0; l0 < pp.nK; l0 += 32) {
+        const int l = l0 + lane;
+        double sv = 0.0, nv = 0.0;
+        if (l < pp.nK)
+            kernel_terms(pp, a, vA[(long long)i * pp.nK + l], vB[(long long)l * pp.nN + j],
+                         mA[(long long)i * pp.nK + l], mB[(long long)l * pp.nN + j], sv, nv);
+        const int cnt = min(32, pp.nK - l0);
+        for (int u = 0; u < cnt; ++u) {
+            S = __dadd_rn(S, __shfl_sync(0xffffffffu, sv, u));
+            N = __dadd_rn(N, __shfl_sync(0xffffffffu, nv, u));
+        }
+    }
+    if (lane == 0) ratio[t] = N > 0.0 ? __ddiv_rn(S, N) : INFINITY;
 }
 
 // mode 1: ratio >= thr;  mode 2: rank (descending ratio, ties to the lower
-// index) below k.  A plan that fell back to W = 1 accelerates nothing.
-__global__ void kernel_mask_kernel(long long T, int mode, double thr, long long k,
-                                   const DevPlan *__restrict__ plan,
-                                   const double *__restrict__ ratio, unsigned char *mask) {
+// index) below k, counted against the ratios staged through shared memory.
+// Ratios are non-negative (or +inf), so their bit patterns order like the
+// values and the O(T^2) rank count runs on the integer pipe.  A plan that fell
+// back to W = 1 accelerates nothing.
+constexpr int kMaskThreads = 128, kMaskChunk = 2048;
+__global__ void __launch_bounds__(kMaskThreads)
+    kernel_mask_kernel(long long T, int mode, double thr, long long k,
+                       const DevPlan *__restrict__ plan, const double *__restrict__ ratio,
+                       unsigned char *mask) {
+    __shared__ unsigned long long chunk[kMaskChunk];
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    if (plan->W < 2) { mask[t] = 0; return; }
-    const double r = ratio[t];
-    if (mode == 1) { mask[t] = r >= thr ? 1 : 0; return; }
-    long long rank = 0;
-    for (long long u = 0; u < T; ++u) {
-        const double ru = ratio[u];
-        rank += (ru > r || (ru == r && u < t)) ? 1 : 0;
+    const bool fell_back = plan->W < 2;      // uniform
+    if (fell_back || mode == 1) {
+        if (t < T) mask[t] = fell_back ? 0 : (ratio[t] >= thr ? 1 : 0);
+        return;
     }
-    mask[t] = rank < k ? 1 : 0;
+    const unsigned long long r =
+        t < T ? (unsigned long long)__double_as_longlong(ratio[t]) : 0ull;
+    long long rank = 0;
+    for (long long c0 = 0; c0 < T; c0 += kMaskChunk) {
+        const int n = (int)min((long long)kMaskChunk, T - c0);
+        __syncthreads();
+        for (int u = threadIdx.x; u < n; u += kMaskThreads)
+            chunk[u] = (unsigned long long)__double_as_longlong(ratio[c0 + u]);
+        __syncthreads();
+        const long long tl = t - c0;         // ties count below this index
+        for (int u = 0; u < n; ++u) {
+            const unsigned long long ru = chunk[u];
+            rank += (ru > r || (ru == r && u < tl)) ? 1 : 0;
+        }
+    }
+    if (t < T) mask[t] = rank < k ? 1 : 0;
 }
 
 }  // namespace
@@ -342,11 +378,12 @@ cudaError_t launch_kernel_control(const PlanParams &pp, const double *mA, const 
                                   int mode, double thr, long long k, double *ratio,
                                   unsigned char *mask, cudaStream_t st) {
     const long long T = (long long)pp.nM * pp.nN;
-    const int g = (int)((T + 255) / 256);
-    kernel_ratio_kernel<<<g, 256, 0, st>>>(pp, mA, vA, mB, vB, plan, ratio);
+    kernel_ratio_kernel<<<(int)((T * 32 + 255) / 256), 256, 0, st>>>(pp, mA, vA, mB, vB, plan,
+                                                                      ratio);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    kernel_mask_kernel<<<g, 256, 0, st>>>(T, mode, thr, k, plan, ratio, mask);
+    kernel_mask_kernel<<<(int)((T + kMaskThreads - 1) / kMaskThreads), kMaskThreads, 0, st>>>(
+        T, mode, thr, k, plan, ratio, mask);
     return cudaGetLastError();
 }
 

@@ -75,34 +75,6 @@ tdg_status scratch_for_current_device(unsigned char **out) {
     return TDG_OK;
 }
 
-typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                             const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                             const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                             CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-tdg_status map2d(CUtensorMap *m, CUtensorMapDataType dt, size_t esz, const void *base,
-                 long long cols, long long rows, long long ld, int bc, int br) {
-    static EncodeFn fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return err(TDG_ECUDA, "cuTensorMapEncodeTiled is not available");
-        fn = (EncodeFn)p;
-    }
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * (long long)esz)};
-    cuuint32_t box[2] = {(cuuint32_t)bc, (cuuint32_t)br};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return err(TDG_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return TDG_OK;
-}
-
 long long rup(long long v, long long m) { return (v + m - 1) / m * m; }
 
 #define ST_TRY(expr)                                                                    \
@@ -177,21 +149,15 @@ tdg_status run_static(bool nA, bool nB, long long M, long long N, long long K, l
         ST_TRY(launch_pack_k<T>(ob, 1, dplan, W, 0, Bbuf, b_ld, b_rows, st));
     }
     const int gform = form == TDG_SYM ? G_SYM : G_ASYM;
-    int bxa, bxb, bk;
-    packed_gemm_boxes(pp.dtype, gform, &bxa, &bxb, &bk);
-    const CUtensorMapDataType dt =
-        sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    CUtensorMap ma, mb;
-    s = map2d(&ma, dt, sizeof(T), Abuf, a_cols, a_rows, a_ld, bxa, bk);
-    if (s != TDG_OK) return s;
-    s = map2d(&mb, dt, sizeof(T), Bbuf, b_cols, b_rows, b_ld, bxb, bk);
-    if (s != TDG_OK) return s;
+    GemmOperands ops{};
+    ops.a = {Abuf, a_cols, a_rows, a_ld};
+    ops.b = {Bbuf, b_cols, b_rows, b_ld};
     GemmArgs<T> g{};
     g.plan = dplan; g.M = M; g.N = N; g.K = K; g.Mrows = a_cols; g.Krows = a_rows;
     g.L = L; g.P = P; g.nM = nM; g.nK = nK; g.nN = nN; g.pair = pair;
     g.C = C; g.ldc = ldc; g.alpha = (T)alpha; g.beta = (T)beta; g.beta_zero = beta == 0.0;
     g.Rbar = nullptr;
-    ST_TRY(launch_packed_gemm<T>(gform, W, g, ma, mb, st));
+    ST_TRY(launch_packed_gemm<T>(gform, W, g, ops, st));
     return TDG_OK;
 }
 

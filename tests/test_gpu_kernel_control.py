@@ -138,6 +138,20 @@ def test_target_mode_with_control_and_epilogue(tdg, orc, rms):
     assert same_bits(C, ref.C)
 
 
+def test_fallback_plan_accelerates_nothing(tdg, orc):
+    """A target no packing can meet: the planner falls back to W = 1, the mask
+    is empty and C is the conventional product."""
+    A, B = inputs((256, 384, 300), 128, "f32", 960)
+    ref = orc.tdgemm(A, B, L=128, W=2, dtype="f32", form="sym", target_db=90.0,
+                     kernel_control=("fraction", 0.5))
+    assert ref.plan.W == 1
+    C, mask, info = run_ctrl(tdg, A, B, L=128, W=2, dtype="f32", target=90.0,
+                             ctrl=("fraction", 0.5))
+    assert info["W_used"] == 1 and not mask.any()
+    assert same_bits(C, ref.C)
+    assert same_bits(C, orc.gemm_plain(A, B, "f32"))
+
+
 def test_control_off_again_and_argument_checks(tdg, orc):
     """Turning control off restores the plain plan's result; invalid settings
     fail with TDG_EINVAL before any device work; the mask before a pack fails
@@ -164,7 +178,8 @@ def test_control_off_again_and_argument_checks(tdg, orc):
             p.set_kernel_control(*bad)
         assert e.value.status == 1
     p.close()
-    for kw in (dict(form="asym", L=128), dict(form="sym", L=64)):
+    for kw in (dict(form="asym", L=128), dict(form="sym", L=64),
+               dict(form="sym", L=128, keep_packed=True)):
         q = tdg.Plan(256, 256, 256, W=2, dtype="f32", bits=6, rep_noise=None, **kw)
         with pytest.raises(TDGemmError) as e:
             q.set_kernel_control("fraction", 0.5)
