@@ -73,7 +73,7 @@ struct tdgemm_plan_s {
     unsigned char *ws = nullptr;
     size_t ws_bytes = 0;
     DevPlan *dplan = nullptr;
-    double *mA, *eA, *mB, *eB, *sA, *sB, *stab;
+    double *mA, *eA, *mB, *eB, *sA, *sB, *stab, *agg;
     void *cA, *cB, *pair;
     void *Abuf, *Bbuf, *Rbar;
     size_t Abuf_bytes, Bbuf_bytes;
@@ -208,6 +208,8 @@ extern "C" tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB,
     const size_t nAblk = (size_t)p->nM * p->nK, nBblk = (size_t)p->nK * p->nN;
     size_t off = 0;
     size_t o_plan = off; off += up(sizeof(DevPlan));
+    size_t o_agg = off;
+    off += up(((size_t)4 * p->nK + (size_t)kLevelRecDoubles * (kMaxW - 1) * kMaxLevels) * 8);
     size_t o_mA = off; off += up(nAblk * 8);
     size_t o_eA = off; off += up(nAblk * 8);
     size_t o_mB = off; off += up(nBblk * 8);
@@ -252,6 +254,7 @@ extern "C" tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB,
         return fail(TDG_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
     }
     p->dplan = (DevPlan *)(p->ws + o_plan);
+    p->agg = (double *)(p->ws + o_agg);
     p->mA = (double *)(p->ws + o_mA); p->eA = (double *)(p->ws + o_eA);
     p->mB = (double *)(p->ws + o_mB); p->eB = (double *)(p->ws + o_eB);
     p->sA = (double *)(p->ws + o_sA); p->sB = (double *)(p->ws + o_sB);
@@ -389,14 +392,14 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
     const bool nA = p->tA == 'N', nB = p->tB == 'N';
     if (p->form != TDG_PLAIN && p->mode != MODE_MANUAL) {
         // stats of op(A): stored rows x cols; op block grid nM x nK
-        CU_TRY(launch_block_stats<T>(A, nA ? p->M : p->K, nA ? p->K : p->M, p->lda, p->L,
-                                     nA ? 0 : 1, p->nK, p->mA, p->eA, p->dplan, st));
-        CU_TRY(launch_block_stats<T>(B, nB ? p->K : p->N, nB ? p->N : p->K, p->ldb, p->L,
-                                     nB ? 0 : 1, p->nN, p->mB, p->eB, p->dplan, st));
+        CU_TRY(launch_block_stats<T>(A, nA ? p->M : p->K, nA ? p->K : p->M, p->lda, nA ? 0 : 1,
+                                     p->nK, p->mA, p->eA, B, nB ? p->K : p->N,
+                                     nB ? p->N : p->K, p->ldb, nB ? 0 : 1, p->nN, p->mB, p->eB,
+                                     p->L, p->dplan, st));
     }
     PlanParams pp = params_of(p);
     const double *stab = p->have_table ? p->stab : nullptr;
-    CU_TRY(launch_planner<T>(pp, p->mA, p->eA, p->mB, p->eB, stab, p->dplan, (T *)p->cA,
+    CU_TRY(launch_planner<T>(pp, p->mA, p->eA, p->mB, p->eB, stab, p->dplan, p->agg, (T *)p->cA,
                              p->sA, (T *)p->cB, p->sB, (T *)p->pair, st));
     if (p->kctrl_mode) {
         CU_TRY(launch_kernel_control(pp, p->mA, p->eA, p->mB, p->eB, p->dplan, p->kctrl_mode,

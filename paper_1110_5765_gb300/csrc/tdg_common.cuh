@@ -12,6 +12,7 @@ namespace tdg {
 constexpr int kUSafe = 50;             // Prop. 1: u_safe = 50
 constexpr int kMaxW = 4;               // packings built: W in 1..4
 constexpr int kMaxLevels = 192;        // R_max candidate levels t in [0, 192)
+constexpr int kLevelRecDoubles = 6;    // workspace per planner candidate (W, level)
 constexpr double kTcIntExact = 16777215.0;  // per-slab |sum| that fp32 holds exactly
 constexpr int kTcIntMaxGamma = 2048;        // integers exactly representable in fp16
 constexpr double kFp8Max = 448.0;           // largest finite E4M3 value

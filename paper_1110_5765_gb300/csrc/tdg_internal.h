@@ -23,16 +23,27 @@ struct PackOperand {
     int L;
 };
 
+// Per L x L block max|x| and sigma^2 of op(A) and op(B), one launch.  Each
+// operand is given as stored (rows_s x cols_s, leading dimension ld) with
+// trans = 1 when op() transposes it; nbc = block columns of op(); results
+// go to mx / var at op() block index i * nbc + j.
 template <typename T>
-cudaError_t launch_block_stats(const T *X, long long rows_s, long long cols_s, long long ld,
-                               int L, int trans, int nbc_op, double *mx, double *ss,
-                               DevPlan *plan, cudaStream_t st);
+cudaError_t launch_block_stats(const T *A, long long rows_a, long long cols_a, long long lda,
+                               int trans_a, int nbc_a, double *mxA, double *varA, const T *B,
+                               long long rows_b, long long cols_b, long long ldb, int trans_b,
+                               int nbc_b, double *mxB, double *varB, int L, DevPlan *plan,
+                               cudaStream_t st);
 
+// Planner: per-slab aggregates into agg (4 nK + kLevelRecDoubles (kMaxW - 1)
+// kMaxLevels doubles of workspace: the aggregates, then one record per
+// candidate (W, level)), the
+// choice of W / z / companders into *plan, then c, s per block and the
+// de-companding factors.
 template <typename T>
 cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double *eA,
                            const double *mB, const double *eB, const double *stab,
-                           DevPlan *plan, T *cA, double *sA, T *cB, double *sB, T *pair,
-                           cudaStream_t st);
+                           DevPlan *plan, double *agg, T *cA, double *sA, T *cB, double *sB,
+                           T *pair, cudaStream_t st);
 
 // Sec. 6 inner-kernel control: per-kernel predicted S/N and the mask of
 // kernels that run packed (mode 1: S/N >= thr; mode 2: the k best).

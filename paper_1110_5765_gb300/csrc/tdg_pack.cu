@@ -379,6 +379,32 @@ Src<T> make_src(const PackOperand<T> &o) {
 
 int capped(long long n) { return (int)max(1LL, min(n, (long long)MAX_CTAS)); }
 
+// Grid of at most `waves` full waves of resident CTAs for `kern` (occupancy
+// x SMs, cached per kernel), so a grid-stride kernel never ends on a partial
+// wave of long-running CTAs and an early exit costs few CTAs.
+int resident_grid(const void *kern, long long n, int waves) {
+    struct Entry { const void *k; int ctas; };
+    static Entry cache[64];
+    static int ncache = 0, sms = 0;
+    int ctas = 0;
+    for (int i = 0; i < ncache; ++i)
+        if (cache[i].k == kern) ctas = cache[i].ctas;
+    if (!ctas) {
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (sms <= 0) sms = 152;
+        }
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0) != cudaSuccess || per < 1)
+            per = 1;
+        ctas = per * sms;
+        if (ncache < 64) cache[ncache++] = {kern, ctas};
+    }
+    return (int)max(1LL, min(n, (long long)ctas * waves));
+}
+
 template <typename T, int W>
 cudaError_t launch_pack_k_w(const PackOperand<T> &o, const DevPlan *plan, int expectW, int wsign,
                             T *out, long long ldo, long long rows_out, cudaStream_t st) {
@@ -390,13 +416,15 @@ cudaError_t launch_pack_k_w(const PackOperand<T> &o, const DevPlan *plan, int ex
     if (o.sx == 1) {
         const int vec_ok = aligned_in && aligned_out && (o.sk % VEC == 0);
         const long long items = rows_out * ((o.X + VEC - 1) / VEC);
-        pack_k_xc_kernel<T, W><<<capped((items + 255) / 256), 256, 0, st>>>(
+        pack_k_xc_kernel<T, W><<<resident_grid((const void *)pack_k_xc_kernel<T, W>,
+                                               (items + 255) / 256, 4), 256, 0, st>>>(
             S, P, plan, expectW, wsign, out, ldo, rows_out, vec_ok);
     } else {
         const int vec_ok = aligned_in && (o.sx % VEC == 0) && o.sk == 1;
         const long long tiles = ((o.X + TILE - 1) / TILE) * ((o.K + o.L - 1) / o.L) *
                                 ((P + TILE - 1) / TILE);
-        pack_k_kc_kernel<T, W><<<capped(tiles), 256, 0, st>>>(S, P, plan, expectW, wsign, out, ldo,
+        pack_k_kc_kernel<T, W><<<resident_grid((const void *)pack_k_kc_kernel<T, W>, tiles, 4), 256,
+                                 0, st>>>(S, P, plan, expectW, wsign, out, ldo,
                                                               rows_out, vec_ok);
     }
     return cudaGetLastError();

@@ -71,50 +71,145 @@ __device__ inline double snr_db(double S, double N) {
     return N <= 0.0 ? INFINITY : 10.0 * log10(S / N);
 }
 
-__global__ void __launch_bounds__(kPlanThreads) planner_kernel(
-    PlanParams pp, const double *__restrict__ mA, const double *__restrict__ vA,
-    const double *__restrict__ mB, const double *__restrict__ vB,
-    const double *__restrict__ stab, DevPlan *plan) {
-    __shared__ double red[4][kPlanThreads];
-    __shared__ double best_n[kPlanThreads];
-    __shared__ int best_t[kPlanThreads];
-    const int tid = threadIdx.x;
-    const int L = pp.L;
+// Per-slab aggregates X_l = sum_i sigma_A,il^2, MA_l = sum_i m_A,il^2,
+// Y_l = sum_j sigma_B,lj^2, MB_l = sum_j m_B,lj^2: one warp per slab on its own
+// SM (GB300's fp64 rate is a small fraction of fp32, so the sums are spread
+// over the GPU rather than serialised on one SM), lanes over i (j), then a
+// fixed xor tree.
+__global__ void __launch_bounds__(32) slab_aggregates_kernel(PlanParams pp,
+                                                             const double *__restrict__ mA,
+                                                             const double *__restrict__ vA,
+                                                             const double *__restrict__ mB,
+                                                             const double *__restrict__ vB,
+                                                             double *__restrict__ agg) {
+    if (pp.mode == MODE_MANUAL) return;
+    const int l = blockIdx.x, lane = threadIdx.x;
+    double X = 0, MA = 0, Y = 0, MB = 0;
+    for (int i = lane; i < pp.nM; i += 32) {
+        X += vA[(long long)i * pp.nK + l];
+        const double m = mA[(long long)i * pp.nK + l];
+        MA += m * m;
+    }
+    for (int j = lane; j < pp.nN; j += 32) {
+        Y += vB[(long long)l * pp.nN + j];
+        const double m = mB[(long long)l * pp.nN + j];
+        MB += m * m;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        X += __shfl_xor_sync(0xffffffffu, X, off);
+        MA += __shfl_xor_sync(0xffffffffu, MA, off);
+        Y += __shfl_xor_sync(0xffffffffu, Y, off);
+        MB += __shfl_xor_sync(0xffffffffu, MB, off);
+    }
+    if (lane == 0) {
+        agg[4 * (long long)l + 0] = X;
+        agg[4 * (long long)l + 1] = MA;
+        agg[4 * (long long)l + 2] = Y;
+        agg[4 * (long long)l + 3] = MB;
+    }
+}
 
-    // ---- per-slab aggregates X_l, Y_l, MA_l, MB_l and their products
-    double S = 0, T1 = 0, T2 = 0, T3 = 0;
+// S / L, T1, T2, T3: products of the per-slab aggregates summed over slabs by
+// one warp (lanes over l, then a fixed xor tree); every caller gets the same
+// bits.
+__device__ inline void slab_totals(const PlanParams &pp, const double *__restrict__ agg,
+                                   double &S, double &T1, double &T2, double &T3) {
+    const int lane = threadIdx.x & 31;
+    S = T1 = T2 = T3 = 0.0;
     if (pp.mode != MODE_MANUAL) {
-        for (int l = tid; l < pp.nK; l += kPlanThreads) {
-            double X = 0, MA = 0, Y = 0, MB = 0;
-            for (int i = 0; i < pp.nM; ++i) {
-                X += vA[(long long)i * pp.nK + l];
-                double m = mA[(long long)i * pp.nK + l];
-                MA += m * m;
-            }
-            for (int j = 0; j < pp.nN; ++j) {
-                Y += vB[(long long)l * pp.nN + j];
-                double m = mB[(long long)l * pp.nN + j];
-                MB += m * m;
-            }
+        for (int l = lane; l < pp.nK; l += 32) {
+            const double X = agg[4 * (long long)l], MA = agg[4 * (long long)l + 1];
+            const double Y = agg[4 * (long long)l + 2], MB = agg[4 * (long long)l + 3];
             S += X * Y;
             T1 += X * MB;
             T2 += Y * MA;
             T3 += MA * MB;
         }
     }
-    red[0][tid] = S; red[1][tid] = T1; red[2][tid] = T2; red[3][tid] = T3;
-    __syncthreads();
-    for (int o = kPlanThreads / 2; o > 0; o >>= 1) {
-        if (tid < o)
-            for (int k = 0; k < 4; ++k) red[k][tid] += red[k][tid + o];
-        __syncthreads();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        S += __shfl_xor_sync(0xffffffffu, S, off);
+        T1 += __shfl_xor_sync(0xffffffffu, T1, off);
+        T2 += __shfl_xor_sync(0xffffffffu, T2, off);
+        T3 += __shfl_xor_sync(0xffffffffu, T3, off);
     }
+}
+
+__device__ inline double rho_of(double T1, double T2) {
+    return (T1 <= 0.0 || T2 <= 0.0) ? 1.0 : sqrt(T2 / T1);
+}
+
+// Target mode, packed forms: every candidate (W, R_max level t) evaluated in
+// full by one lane (companders, z, representation noise, model noise and
+// SNR), 32 candidates per CTA spread over SMs: fp64 divisions, square roots
+// and logarithms are slow on GB300 and would serialise on one SM.  n < 0
+// marks a level without usable companders or representation-noise value.
+struct LevelRec {
+    double n, pred, s;
+    long long R;
+    int gA, gB, q, Wef;
+};
+static_assert(sizeof(LevelRec) == kLevelRecDoubles * sizeof(double), "planner workspace record");
+
+__global__ void __launch_bounds__(32) level_kernel(PlanParams pp, const double *__restrict__ agg,
+                                                   const double *__restrict__ stab,
+                                                   LevelRec *__restrict__ res) {
+    const int L = pp.L;
+    int t_lo = 0;
+    while (r_level(t_lo) < L) ++t_lo;
+    const int t_hi = t_max_for(pp.p);
+    const int nlev = t_hi - t_lo + 1;
+    const int per_w = (nlev + 31) / 32;                 // CTAs per W
+    const int W = pp.Wreq - (int)blockIdx.x / per_w;
+    const int t = t_lo + ((int)blockIdx.x % per_w) * 32 + (int)threadIdx.x;
+    DevPlan a{};
+    double S, T1, T2, T3;
+    slab_totals(pp, agg, S, T1, T2, T3);
+    if (W < 2 || t > t_hi) return;
+    a.S = (double)L * S; a.T1 = T1; a.T2 = T2; a.T3 = T3;
+    const double rho = rho_of(T1, T2);
+    LevelRec r{};
+    r.n = -1.0;
+    const long long Rt = r_level(t);
+    r.q = q_for(Rt);
+    split_gammas(Rt, L, rho, r.gA, r.gB);
+    if (r.gA >= 1) {
+        r.R = (long long)L * r.gA * r.gB;
+        r.Wef = w_ef(r.R, r.q, pp.p);
+        double sv = -1.0;
+        if (W <= r.Wef) sv = 0.0;
+        else if (stab && t >= pp.t0 && t < pp.t0 + pp.nt) sv = stab[(W - 2) * pp.nt + (t - pp.t0)];
+        if (sv >= 0.0) {
+            r.n = model_noise(a, L, r.gA, r.gB, sv, pp.noise_rms);
+            r.pred = snr_db(a.S, r.n);
+            r.s = sv > 0.0 ? sv : 0.0;
+        }
+    }
+    res[(W - 2) * kMaxLevels + t] = r;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) planner_kernel(
+    PlanParams pp, const double *__restrict__ agg, const double *__restrict__ stab,
+    const LevelRec *__restrict__ res, DevPlan *plan) {
+    __shared__ unsigned long long best_n[kPlanThreads];
+    __shared__ int best_t[kPlanThreads];
+    __shared__ double tot[4];
+    const int tid = threadIdx.x;
+    const int L = pp.L;
+
+    if (tid < 32) {
+        double S, T1, T2, T3;
+        slab_totals(pp, agg, S, T1, T2, T3);
+        if (tid == 0) { tot[0] = S; tot[1] = T1; tot[2] = T2; tot[3] = T3; }
+    }
+    __syncthreads();
     DevPlan a;
-    a.S = (double)L * red[0][0];
-    a.T1 = red[1][0];
-    a.T2 = red[2][0];
-    a.T3 = red[3][0];
-    const double rho = (a.T1 <= 0.0 || a.T2 <= 0.0) ? 1.0 : sqrt(a.T2 / a.T1);
+    a.S = (double)L * tot[0];
+    a.T1 = tot[1];
+    a.T2 = tot[2];
+    a.T3 = tot[3];
+    const double rho = rho_of(a.T1, a.T2);
     a.status = 0;
     a.level = -1;
     a.pred_snr = NAN;
@@ -165,32 +260,23 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
         DevPlan first{};
         bool have_first = false;
         for (int W = pp.Wreq; W >= 2 && !chosen; --W) {
-            double bn = INFINITY;
+            // argmin of N over the levels (ties to the lower level); N >= 0,
+            // so its bit pattern orders like its value (integer compares)
+            unsigned long long bn = ~0ull;
             int bt = -1;
             for (int t = t_lo + tid; t <= t_hi; t += kPlanThreads) {
-                long long Rt = r_level(t);
-                int q = q_for(Rt);
-                int gA, gB;
-                split_gammas(Rt, L, rho, gA, gB);
-                if (gA < 1) continue;
-                long long R = (long long)L * gA * gB;
-                double s = -1.0;
-                if (W <= w_ef(R, q, pp.p)) {
-                    s = 0.0;
-                } else if (stab && t >= pp.t0 && t < pp.t0 + pp.nt) {
-                    s = stab[(W - 2) * pp.nt + (t - pp.t0)];
-                }
-                if (s < 0.0) continue;
-                double n = model_noise(a, L, gA, gB, s, pp.noise_rms);
-                if (n < bn) { bn = n; bt = t; }
+                const double n = res[(W - 2) * kMaxLevels + t].n;   // level_kernel
+                if (n < 0.0) continue;
+                const unsigned long long nb = (unsigned long long)__double_as_longlong(n);
+                if (nb < bn) { bn = nb; bt = t; }
             }
             best_n[tid] = bn;
             best_t[tid] = bt;
             __syncthreads();
             for (int o = kPlanThreads / 2; o > 0; o >>= 1) {
                 if (tid < o) {
-                    double n2 = best_n[tid + o];
-                    int t2 = best_t[tid + o];
+                    const unsigned long long n2 = best_n[tid + o];
+                    const int t2 = best_t[tid + o];
                     if (t2 >= 0 && (best_t[tid] < 0 || n2 < best_n[tid] ||
                                     (n2 == best_n[tid] && t2 < best_t[tid]))) {
                         best_n[tid] = n2;
@@ -200,24 +286,19 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
                 __syncthreads();
             }
             const int t = best_t[0];
-            const double n = best_n[0];
             __syncthreads();
             if (t < 0) continue;
+            const LevelRec &r = res[(W - 2) * kMaxLevels + t];
             DevPlan c = a;
-            long long Rt = r_level(t);
             c.W = W;
-            c.q = q_for(Rt);
-            split_gammas(Rt, L, rho, c.gA, c.gB);
-            c.R = (long long)L * c.gA * c.gB;
-            c.Wef = w_ef(c.R, c.q, pp.p);
+            c.q = r.q;
+            c.gA = r.gA;
+            c.gB = r.gB;
+            c.R = r.R;
+            c.Wef = r.Wef;
             c.level = t;
-            c.pred_snr = snr_db(a.S, n);
-            {
-                double sc = 0.0;
-                if (!(c.W <= w_ef(c.R, c.q, pp.p)) && stab && t >= pp.t0 && t < pp.t0 + pp.nt)
-                    sc = stab[(c.W - 2) * pp.nt + (t - pp.t0)];
-                c.s_rep = sc > 0.0 ? sc : 0.0;
-            }
+            c.pred_snr = r.pred;
+            c.s_rep = r.s;
             if (!have_first) { first = c; have_first = true; }
             if (c.pred_snr >= pp.target_db) { a = c; chosen = true; }
         }
@@ -390,9 +471,27 @@ cudaError_t launch_kernel_control(const PlanParams &pp, const double *mA, const 
 template <typename T>
 cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double *eA,
                            const double *mB, const double *eB, const double *stab,
-                           DevPlan *plan, T *cA, double *sA, T *cB, double *sB, T *pair,
-                           cudaStream_t st) {
-    planner_kernel<<<1, kPlanThreads, 0, st>>>(pp, mA, eA, mB, eB, stab, plan);
+                           DevPlan *plan, double *agg, T *cA, double *sA, T *cB, double *sB,
+                           T *pair, cudaStream_t st) {
+    // agg: 4 nK per-slab aggregates, then one record per candidate (W, level)
+    LevelRec *res = reinterpret_cast<LevelRec *>(agg + 4 * (long long)pp.nK);
+    if (pp.mode != MODE_MANUAL) {
+        slab_aggregates_kernel<<<pp.nK, 32, 0, st>>>(pp, mA, eA, mB, eB, agg);
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
+    if (pp.mode == MODE_TARGET && (pp.form == TDG_SYM || pp.form == TDG_ASYM)) {
+        int t_lo = 0;
+        while (r_level(t_lo) < pp.L) ++t_lo;
+        const int nlev = (pp.p == 24 ? 4 * 24 : 4 * 40) - t_lo + 1;
+        const int ctas = (pp.Wreq - 1) * ((nlev + 31) / 32);
+        if (ctas > 0) {
+            level_kernel<<<ctas, 32, 0, st>>>(pp, agg, stab, res);
+            cudaError_t e1 = cudaGetLastError();
+            if (e1 != cudaSuccess) return e1;
+        }
+    }
+    planner_kernel<<<1, kPlanThreads, 0, st>>>(pp, agg, stab, res, plan);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     long long nblk = (long long)pp.nM * pp.nK + (long long)pp.nK * pp.nN;
@@ -408,11 +507,11 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
 
 template cudaError_t launch_planner<float>(const PlanParams &, const double *, const double *,
                                            const double *, const double *, const double *,
-                                           DevPlan *, float *, double *, float *, double *,
-                                           float *, cudaStream_t);
+                                           DevPlan *, double *, float *, double *, float *,
+                                           double *, float *, cudaStream_t);
 template cudaError_t launch_planner<double>(const PlanParams &, const double *, const double *,
                                             const double *, const double *, const double *,
                                             DevPlan *, double *, double *, double *, double *,
-                                            double *, cudaStream_t);
+                                            double *, double *, cudaStream_t);
 
 }  // namespace tdg

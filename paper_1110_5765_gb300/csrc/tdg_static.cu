@@ -101,6 +101,8 @@ tdg_status run_static(bool nA, bool nB, long long M, long long N, long long K, l
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
     const size_t o_plan = take(sizeof(DevPlan));
+    const size_t o_agg =
+        take(((size_t)4 * nK + (size_t)kLevelRecDoubles * (kMaxW - 1) * kMaxLevels) * 8);
     const size_t o_mA = take(nA_blk * 8), o_eA = take(nA_blk * 8);
     const size_t o_mB = take(nB_blk * 8), o_eB = take(nB_blk * 8);
     const size_t o_sA = take(nA_blk * 8), o_sB = take(nB_blk * 8);
@@ -117,6 +119,7 @@ tdg_status run_static(bool nA, bool nB, long long M, long long N, long long K, l
     tdg_status s = scratch_for_current_device(&ws);
     if (s != TDG_OK) return s;
     DevPlan *dplan = (DevPlan *)(ws + o_plan);
+    double *agg = (double *)(ws + o_agg);
     double *mA = (double *)(ws + o_mA), *eA = (double *)(ws + o_eA);
     double *mB = (double *)(ws + o_mB), *eB = (double *)(ws + o_eB);
     double *sA = (double *)(ws + o_sA), *sB = (double *)(ws + o_sB);
@@ -125,17 +128,16 @@ tdg_status run_static(bool nA, bool nB, long long M, long long N, long long K, l
 
     // the plan record carries the device status and non-finite flag: start at zero
     ST_TRY(cudaMemsetAsync(dplan, 0, sizeof(DevPlan), st));
-    ST_TRY(launch_block_stats<T>(A, nA ? M : K, nA ? K : M, lda, L, nA ? 0 : 1, nK, mA, eA,
-                                 dplan, st));
-    ST_TRY(launch_block_stats<T>(B, nB ? K : N, nB ? N : K, ldb, L, nB ? 0 : 1, nN, mB, eB,
-                                 dplan, st));
+    ST_TRY(launch_block_stats<T>(A, nA ? M : K, nA ? K : M, lda, nA ? 0 : 1, nK, mA, eA, B,
+                                 nB ? K : N, nB ? N : K, ldb, nB ? 0 : 1, nN, mB, eB, L, dplan,
+                                 st));
     PlanParams pp{};
     pp.mode = MODE_FIXED; pp.form = form; pp.dtype = sizeof(T) == 8 ? TDG_F64 : TDG_F32;
     pp.L = L; pp.Wreq = W; pp.p = sizeof(T) == 8 ? 53 : 24; pp.bits = bits;
     pp.allow_fallback = 0; pp.noise_rms = 0; pp.target_db = NAN;
     pp.nM = nM; pp.nK = nK; pp.nN = nN; pp.M = M; pp.N = N; pp.K = K;
     pp.t0 = 0; pp.nt = 0;
-    ST_TRY(launch_planner<T>(pp, mA, eA, mB, eB, nullptr, dplan, cA, sA, cB, sB, pair, st));
+    ST_TRY(launch_planner<T>(pp, mA, eA, mB, eB, nullptr, dplan, agg, cA, sA, cB, sB, pair, st));
     PackOperand<T> oa{}, ob{};
     oa.src = A; oa.X = M; oa.K = K; oa.L = L; oa.c = cA; oa.cx = nK; oa.cl = 1;
     if (nA) { oa.sx = lda; oa.sk = 1; } else { oa.sx = 1; oa.sk = lda; }

@@ -4,9 +4,9 @@
 // reorder; Sec. 5.B adds sigma.  Here one CTA reads one L x L tile of the
 // stored matrix with 16-byte vector loads (one HBM pass) and produces
 //   max|x|   exact,
-//   sigma^2  sum x^2 / (valid elements), about zero; the sum in fp64 (fp32
-//            inputs: per-thread double-float accumulation of exact squares,
-//            then an fp64 tree).
+//   sigma^2  sum x^2 / (valid elements), about zero (fp32 inputs:
+//            double-float accumulation of exact squares per thread and a
+//            double-float tree over the block; fp64 inputs: fp64 throughout).
 // Non-finite inputs raise TDG_ENONFINITE in the plan's device status.
 #include "tdg_common.cuh"
 #include "tdg_internal.h"
@@ -40,6 +40,17 @@ __device__ inline void add_sq(Acc &a, int lane, float x) {
     a.bad |= (b >= 0x7f800000u);
 }
 
+// (hi, lo) += (bh, bl) in double-float arithmetic (TwoSum of the high parts,
+// low parts added to the error, then renormalised)
+__device__ inline void df_add(float &hi, float &lo, float bh, float bl) {
+    const float s = __fadd_rn(hi, bh);
+    const float v = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(bh, v));
+    const float t = __fadd_rn(e, __fadd_rn(lo, bl));
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
 __device__ inline void add_sq(Acc &a, int lane, double x) {
     a.d[lane & 1] = __fma_rn(x, x, a.d[lane & 1]);
     unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
@@ -47,25 +58,39 @@ __device__ inline void add_sq(Acc &a, int lane, double x) {
     a.bad |= (b >= 0x7ff0000000000000ull);
 }
 
+// One operand: the stored matrix rows_s x cols_s (leading dimension ld),
+// op() transposed when trans; block (bi, bj) of the stored matrix is block
+// (bj, bi) of op() then.  nbc_op = block columns of op().
 template <typename T>
-__global__ void __launch_bounds__(256) block_stats_kernel(const T *__restrict__ X,
-                                                          long long rows_s, long long cols_s,
-                                                          long long ld, int L, int trans,
-                                                          int nbc_op, double *__restrict__ mx,
-                                                          double *__restrict__ var,
+struct StatsOp {
+    const T *X;
+    long long rows_s, cols_s, ld;
+    int trans, nbc_op, nbc_s;       // nbc_s = block columns of the stored matrix
+    long long nblk;                 // blocks of the stored matrix
+    double *mx, *var;
+};
+
+// Both operands in one launch: CTAs [0, A.nblk) take A's blocks, the rest B's.
+template <typename T>
+__global__ void __launch_bounds__(256) block_stats_kernel(StatsOp<T> A, StatsOp<T> B, int L,
                                                           DevPlan *plan) {
     constexpr int VEC = 16 / sizeof(T);
-    const int bj = blockIdx.x, bi = blockIdx.y;
-    const long long r0b = (long long)bi * L, c0 = (long long)bj * L;
-    const int rn = (int)min((long long)L, rows_s - r0b);
-    const int cn = (int)min((long long)L, cols_s - c0);
+    const bool isA = (long long)blockIdx.x < A.nblk;
+    const StatsOp<T> &o = isA ? A : B;
+    const long long blk = isA ? (long long)blockIdx.x : (long long)blockIdx.x - A.nblk;
+    const long long bi = blk / o.nbc_s, bj = blk - bi * o.nbc_s;
+    const T *__restrict__ X = o.X;
+    const long long ld = o.ld;
+    const long long r0b = bi * L, c0 = bj * L;
+    const int rn = (int)min((long long)L, o.rows_s - r0b);
+    const int cn = (int)min((long long)L, o.cols_s - c0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const bool vec_ok = (ld % VEC == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
 
     Acc a{{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, {0.0, 0.0}, 0ull, 0};
-    // rows in batches of four per warp so four 16-byte loads are in flight
+    // rows in batches of eight per warp so eight 16-byte loads are in flight
     // before any of them is consumed
-    constexpr int RB = 4;
+    constexpr int RB = 8;
     for (int c = lane * VEC; c < cn; c += 32 * VEC) {
         const bool vec = vec_ok && c + VEC <= cn;
         for (int r0 = warp; r0 < rn; r0 += RB * nwarp) {
@@ -93,41 +118,57 @@ __global__ void __launch_bounds__(256) block_stats_kernel(const T *__restrict__ 
                 for (int e = 0; e < VEC; ++e) add_sq(a, e, v[u][e]);
         }
     }
-    double s;
-    if (sizeof(T) == 4) {
-        s = 0.0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) s += (double)a.hi[q] + (double)a.lo[q];
-    } else {
-        s = a.d[0] + a.d[1];
-    }
-    double m = (sizeof(T) == 4) ? (double)__uint_as_float((unsigned int)a.mbits)
-                                : __longlong_as_double((long long)a.mbits);
-    int bad = a.bad;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    }
-    __shared__ double sh_s[32], sh_m[32];
+    // block sum of squares and max|x|: fp32 inputs reduce (hi, lo) float pairs
+    // with double-float additions and float bit patterns (GB300 runs fp64 at a
+    // small fraction of the fp32 rate, so fp64 appears only once per block);
+    // fp64 inputs reduce in fp64
+    __shared__ float sh_h[32], sh_l[32];
+    __shared__ double sh_d[32];
+    __shared__ unsigned long long sh_m[32];
     __shared__ int sh_b[32];
-    if (lane == 0) { sh_s[warp] = s; sh_m[warp] = m; sh_b[warp] = bad; }
+    float hi = 0.f, lo = 0.f;
+    double d = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        hi = a.hi[0]; lo = a.lo[0];
+#pragma unroll
+        for (int q = 1; q < 4; ++q) df_add(hi, lo, a.hi[q], a.lo[q]);
+    } else {
+        d = a.d[0] + a.d[1];
+    }
+    unsigned long long mb = a.mbits;
+    int bad = a.bad;
+    auto warp_reduce = [&]() {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            if constexpr (sizeof(T) == 4) {
+                const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
+                const float ol = __shfl_xor_sync(0xffffffffu, lo, off);
+                df_add(hi, lo, oh, ol);
+            } else {
+                d += __shfl_xor_sync(0xffffffffu, d, off);
+            }
+            mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, mb, off));
+            bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+        }
+    };
+    warp_reduce();
+    if (lane == 0) { sh_h[warp] = hi; sh_l[warp] = lo; sh_d[warp] = d; sh_m[warp] = mb; sh_b[warp] = bad; }
     __syncthreads();
     if (warp == 0) {
-        s = lane < nwarp ? sh_s[lane] : 0.0;
-        m = lane < nwarp ? sh_m[lane] : 0.0;
-        bad = lane < nwarp ? sh_b[lane] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-            m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-            bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-        }
+        const bool in = lane < nwarp;
+        hi = in ? sh_h[lane] : 0.f;
+        lo = in ? sh_l[lane] : 0.f;
+        d = in ? sh_d[lane] : 0.0;
+        mb = in ? sh_m[lane] : 0ull;
+        bad = in ? sh_b[lane] : 0;
+        warp_reduce();
         if (lane == 0) {
-            long long idx = trans ? (long long)bj * nbc_op + bi : (long long)bi * nbc_op + bj;
-            mx[idx] = m;
-            var[idx] = s / ((double)rn * (double)cn);   // sigma^2 about zero
+            const double ssum = sizeof(T) == 4 ? (double)hi + (double)lo : d;
+            const double m = sizeof(T) == 4 ? (double)__uint_as_float((unsigned int)mb)
+                                            : __longlong_as_double((long long)mb);
+            long long idx = o.trans ? bj * o.nbc_op + bi : bi * o.nbc_op + bj;
+            o.mx[idx] = m;
+            o.var[idx] = ssum / ((double)rn * (double)cn);   // sigma^2 about zero
             if (bad) atomicExch(&plan->nonfinite, 1);
         }
     }
@@ -136,20 +177,37 @@ __global__ void __launch_bounds__(256) block_stats_kernel(const T *__restrict__ 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_block_stats(const T *X, long long rows_s, long long cols_s, long long ld,
-                               int L, int trans, int nbc_op, double *mx, double *var,
-                               DevPlan *plan, cudaStream_t st) {
-    dim3 grid(cdiv_i(cols_s, L), cdiv_i(rows_s, L));
-    block_stats_kernel<T><<<grid, 256, 0, st>>>(X, rows_s, cols_s, ld, L, trans, nbc_op, mx, var,
-                                                plan);
+static StatsOp<T> stats_op(const T *X, long long rows_s, long long cols_s, long long ld, int L,
+                           int trans, int nbc_op, double *mx, double *var) {
+    StatsOp<T> o;
+    o.X = X; o.rows_s = rows_s; o.cols_s = cols_s; o.ld = ld;
+    o.trans = trans; o.nbc_op = nbc_op;
+    o.nbc_s = cdiv_i(cols_s, L);
+    o.nblk = (long long)cdiv_i(rows_s, L) * o.nbc_s;
+    o.mx = mx; o.var = var;
+    return o;
+}
+
+template <typename T>
+cudaError_t launch_block_stats(const T *A, long long rows_a, long long cols_a, long long lda,
+                               int trans_a, int nbc_a, double *mxA, double *varA, const T *B,
+                               long long rows_b, long long cols_b, long long ldb, int trans_b,
+                               int nbc_b, double *mxB, double *varB, int L, DevPlan *plan,
+                               cudaStream_t st) {
+    StatsOp<T> oa = stats_op(A, rows_a, cols_a, lda, L, trans_a, nbc_a, mxA, varA);
+    StatsOp<T> ob = stats_op(B, rows_b, cols_b, ldb, L, trans_b, nbc_b, mxB, varB);
+    const long long nb = oa.nblk + ob.nblk;
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    block_stats_kernel<T><<<(unsigned)nb, 256, 0, st>>>(oa, ob, L, plan);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_block_stats<float>(const float *, long long, long long, long long,
-                                               int, int, int, double *, double *, DevPlan *,
-                                               cudaStream_t);
-template cudaError_t launch_block_stats<double>(const double *, long long, long long,
-                                                long long, int, int, int, double *, double *,
-                                                DevPlan *, cudaStream_t);
+#define TDG_STATS_INST(T)                                                                     \
+    template cudaError_t launch_block_stats<T>(const T *, long long, long long, long long, int, \
+                                               int, double *, double *, const T *, long long, \
+                                               long long, long long, int, int, double *,        \
+                                               double *, int, DevPlan *, cudaStream_t);
+TDG_STATS_INST(float)
+TDG_STATS_INST(double)
 
 }  // namespace tdg

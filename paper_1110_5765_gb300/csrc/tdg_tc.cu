@@ -11,14 +11,18 @@
 // C = sum_l (s_A,il s_B,lj) * (A~_l B~_l^T), slabs l of L k-values.
 //
 // CTA tile 128 x 256, one persistent CTA per SM (192 KB of shared memory) that
-// walks its share of the output tiles, the pipeline running on across tiles:
+// walks its share of the output tiles, the pipeline running on across tiles.
+// CTAs run in clusters of two on vertically adjacent tiles (same 256 columns
+// of B~): each CTA loads its own 128 rows of A~ and one half of the B~ tile,
+// multicast into both CTAs' shared memory, so a pair reads B~ once from L2.
 //   warp 0      allocates 512 TMEM columns; lane 0 streams 128-byte-wide k
-//               boxes of A~ (128 rows) and B~ (256 rows) with 2-D TMA
-//               (128-byte swizzle, no multicast) into a 4-deep ring;
+//               boxes of A~ (128 rows) and its half of B~ (128 rows, to both
+//               CTAs) with 2-D TMA (128-byte swizzle) into a 4-deep ring;
 //   warp 1      lane 0 issues tcgen05.mma (M = 128, N = 256) into one of two
 //               TMEM accumulators, a fresh accumulation per slab, and
-//               commits to mbarriers that free ring stages and hand a full
-//               slab to the epilogue;
+//               commits to mbarriers that free ring stages (in both CTAs of
+//               the pair: a stage is refilled once both have consumed it) and
+//               hand a full slab to the epilogue;
 //   warps 2..17 epilogue: each thread owns one output row and 64 columns;
 //               per slab it reads its TMEM lane (tcgen05.ld), applies
 //               C_acc = fma(r, s_A s_B, C_acc) in fp32 and releases the
@@ -80,6 +84,39 @@ __device__ inline void mma(uint32_t dtmem, uint64_t ad, uint64_t bd, int accumul
     }
 }
 
+// the same commit, arriving on the mbarrier at this offset in every CTA of
+// the cluster named in mask
+__device__ inline void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+// 2-D TMA load written to this offset in every CTA of the cluster named in
+// mask, each completing bytes on its own mbarrier at bar's offset
+__device__ inline void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                      int y, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+        : "memory");
+}
+
+__device__ inline uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// every thread of both CTAs of the cluster
+__device__ inline void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ inline void mma_commit(uint64_t *bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -131,26 +168,29 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // persistent CTAs: tile k of this CTA is blockIdx.x + k * gridDim.x (row-major
-    // over 128 x 256 output tiles)
+    // persistent clusters of two: pair k of cluster c is c + k * (clusters),
+    // row-major over pairs of vertically adjacent 128 x 256 output tiles; this
+    // CTA takes the upper (rank 0) or lower (rank 1) tile of each pair
+    const uint32_t rank = cluster_rank();
+    const int cid = (int)blockIdx.x >> 1, ncl = (int)gridDim.x >> 1;
     const int tiles_n = (int)((g.N + BN - 1) / BN), tiles_m = (int)((g.M + BM - 1) / BM);
-    const int ntiles = tiles_n * tiles_m;
-    const int my_tiles =
-        ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int npairs = tiles_n * ((tiles_m + 1) / 2);
+    const int my_tiles = npairs > cid ? (npairs - 1 - cid) / ncl + 1 : 0;
     const int slab_stages = g.L / BK;
     const int nslab = g.nK;
     const int per_tile = nslab * slab_stages;
     const int total = my_tiles * per_tile;
     auto tile_origin = [&](int k, long long &m0, long long &n0) {
-        const int t = (int)blockIdx.x + k * (int)gridDim.x;
-        m0 = (long long)(t / tiles_n) * BM;
+        const int t = cid + k * ncl;
+        m0 = (long long)(2 * (t / tiles_n) + (int)rank) * BM;   // may pass M: zero rows
         n0 = (long long)(t % tiles_n) * BN;
     };
+    constexpr uint16_t kPair = 0x3;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], 2);         // both CTAs' MMAs release the stage
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -167,7 +207,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
+    // both CTAs' barriers exist before either multicasts or commits into them
+    cluster_sync();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -190,9 +231,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const int kx = l * g.L + ks * BK;
                 long long m0, n0;
                 tile_origin(kt, m0, n0);
+                // own A~ rows; this CTA's half of B~ into both CTAs (the other
+                // half arrives from the peer): STAGE_A + STAGE_B bytes per CTA
                 mbar_arrive_expect_tx(&full[stage], STAGE_A + STAGE_B);
                 tma_load_2d(sA + stage * STAGE_A, &mapA, &full[stage], kx, (int)m0);
-                tma_load_2d(sB + stage * STAGE_B, &mapB, &full[stage], kx, (int)n0);
+                tma_load_2d_mc(sB + stage * STAGE_B + rank * (STAGE_B / 2), &mapB, &full[stage],
+                               kx, (int)(n0 + rank * (BN / 2)), kPair);
             }
             // every copy issued must land before the CTA can exit
             for (int k = max(0, it - STAGES); k < it; ++k)
@@ -225,7 +269,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         const uint64_t adv = (uint64_t)((kk * KSTEP_BYTES) >> 4);
                         mma<FP8>(d, ad + adv, bd + adv, (ks | kk) != 0);
                     }
-                    mma_commit(&empty[stage]);          // frees the stage when done
+                    mma_commit_mc(&empty[stage], kPair);   // frees the stage in both CTAs
                 }
                 if (!ok) break;
                 mma_commit(&acc_full[b]);               // the slab is complete in TMEM
@@ -234,8 +278,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);
                 *abort_flag = 1;
             }
-            // wait for this thread's last MMAs before the TMEM can be freed
-            if (it > 0) mbar_wait_bounded(&empty[(it - 1) % STAGES], ((it - 1) / STAGES) & 1);
+            // the last use of every stage released by both CTAs: this thread's
+            // MMAs are done (TMEM can be freed) and the peer's commits into
+            // this CTA's barriers have landed (it may exit)
+            for (int k = max(0, it - STAGES); k < it; ++k)
+                mbar_wait_bounded(&empty[k % STAGES], (k / STAGES) & 1);
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -317,7 +364,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
 
     tc_fence_before();
-    __syncthreads();
+    // neither CTA leaves while the other may still write into it
+    cluster_sync();
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -328,44 +376,48 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 }  // namespace
 
+template <int FP8>
+static cudaError_t launch_tc(const TcArgs &a, const CUtensorMap &mapA, const CUtensorMap &mapB,
+                             cudaStream_t st) {
+    auto kern = tc_gemm_kernel<FP8>;
+    static int max_clusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(NUM_THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (!max_clusters) {
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cfg.gridDim = dim3((unsigned)max(2, sms & ~1));
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, (void *)kern, &cfg);
+        if (e != cudaSuccess) return e;
+        max_clusters = max(1, n);
+    }
+    const long long pairs = ((a.N + BN - 1) / BN) * (((a.M + BM - 1) / BM + 1) / 2);
+    cfg.gridDim = dim3((unsigned)(2 * std::min<long long>(pairs, max_clusters)));
+    return cudaLaunchKernelEx(&cfg, kern, mapA, mapB, a);
+}
+
 cudaError_t launch_tc_gemm(int fp8, const TcArgs &a, const CUtensorMap &mapA,
                            const CUtensorMap &mapB, cudaStream_t st) {
-    static int num_sms = 0;
-    if (!num_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (num_sms <= 0) num_sms = 1;
-    }
-    const long long tiles = ((a.N + BN - 1) / BN) * ((a.M + BM - 1) / BM);
-    dim3 grid((unsigned)std::min<long long>(tiles, num_sms));
-    if (fp8) {
-        static bool set = false;
-        if (!set) {
-            cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<1>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)SMEM_BYTES);
-            if (e != cudaSuccess) return e;
-            set = true;
-        }
-        tc_gemm_kernel<1><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(mapA, mapB, a);
-    } else {
-        static bool set = false;
-        if (!set) {
-            cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<0>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)SMEM_BYTES);
-            if (e != cudaSuccess) return e;
-            set = true;
-        }
-        tc_gemm_kernel<0><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(mapA, mapB, a);
-    }
-    return cudaGetLastError();
+    return fp8 ? launch_tc<1>(a, mapA, mapB, st) : launch_tc<0>(a, mapA, mapB, st);
 }
 
 void tc_gemm_boxes(int fp8, int *box_rows_a, int *box_rows_b, int *box_k) {
     *box_rows_a = BM;
-    *box_rows_b = BN;
+    *box_rows_b = BN / 2;      // each CTA of a pair loads half of the B~ tile
     *box_k = fp8 ? 128 : 64;
 }
 
