@@ -56,6 +56,7 @@ struct Vec4<double> {
 };
 
 __device__ inline float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 __device__ inline double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ inline float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ inline double mul_rn(double a, double b) { return __dmul_rn(a, b); }
@@ -63,6 +64,37 @@ __device__ inline float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ inline double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 __device__ inline float rint_t(float a) { return rintf(a); }
 __device__ inline double rint_t(double a) { return rint(a); }
+
+// acc[i][j] = fma(a[i], b[j], acc[i][j]) for a TM x TN register tile.  For
+// fp32, adjacent columns go through one packed fma.rn.f32x2 (two IEEE fused
+// multiply-adds, each rounded like fma.rn.f32: the same bits as the scalar
+// form), which halves the FMA instructions the SM sub-partitions must issue.
+template <typename T, int TM, int TN>
+__device__ inline void outer_fma(T (&acc)[TM][TN], const T (&a)[TM], const T (&b)[TN]) {
+    if constexpr (sizeof(T) == 4 && TN % 2 == 0) {
+        uint64_t b2[TN / 2];
+#pragma unroll
+        for (int jp = 0; jp < TN / 2; ++jp)
+            asm("mov.b64 %0, {%1, %2};" : "=l"(b2[jp]) : "f"(b[2 * jp]), "f"(b[2 * jp + 1]));
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            uint64_t a2;
+            asm("mov.b64 %0, {%1, %1};" : "=l"(a2) : "f"(a[i]));
+#pragma unroll
+            for (int jp = 0; jp < TN / 2; ++jp) {
+                uint64_t c2;
+                asm("mov.b64 %0, {%1, %2};" : "=l"(c2) : "f"(acc[i][2 * jp]), "f"(acc[i][2 * jp + 1]));
+                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c2) : "l"(a2), "l"(b2[jp]));
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[i][2 * jp]), "=f"(acc[i][2 * jp + 1]) : "l"(c2));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = fma_rn(a[i], b[j], acc[i][j]);
+    }
+}
 __device__ inline float pow2_t(float, int e) { return scalbnf(1.0f, e); }
 
 // Round to nearest, ties to even, on the FMA/ALU pipes: for |x| < 2^23,
@@ -334,10 +366,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
 #pragma unroll
                     for (int hj = 0; hj < CG; ++hj)
                         Vec4<T>::load(Bs + kk * BN + hj * (BN / CG) + tx * 4, b + 4 * hj);
-#pragma unroll
-                    for (int i = 0; i < TM; ++i)
-#pragma unroll
-                        for (int j = 0; j < TN; ++j) acc[i][j] = fma_rn(a[i], b[j], acc[i][j]);
+                    outer_fma(acc, a, b);
                 }
             } else {
                 for (int kk = 0; kk < kcount; ++kk) {
@@ -348,10 +377,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
 #pragma unroll
                     for (int hj = 0; hj < CG; ++hj)
                         Vec4<T>::load(Bs + kk * BN + hj * (BN / CG) + tx * 4, b + 4 * hj);
-#pragma unroll
-                    for (int i = 0; i < TM; ++i)
-#pragma unroll
-                        for (int j = 0; j < TN; ++j) acc[i][j] = fma_rn(a[i], b[j], acc[i][j]);
+                    outer_fma(acc, a, b);
                 }
             }
         }
