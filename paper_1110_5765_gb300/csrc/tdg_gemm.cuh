@@ -400,6 +400,46 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
             for (int hj = 0; hj < CG; ++hj)
                 prs[pi][hj] = __ldg(pl_tab + (long long)iblk[FORM == G_ASYM ? pi : 4 * pi] * g.nN + jblk[hj]);
         float v[16];
+        if constexpr (FORM == G_SYM && TMEMC && !KEEP && TN % 2 == 0) {
+            // eqs. 9-10 and the fma into the running sum on adjacent column
+            // pairs (same factor, adjacent TMEM columns): the products and
+            // fmas as packed f32x2 operations, each lane rounded as the
+            // scalar form
+            uint64_t z2, nq2;
+            asm("mov.b64 %0, {%1, %1};" : "=l"(z2) : "f"((float)z));
+            asm("mov.b64 %0, {%1, %1};" : "=l"(nq2) : "f"(-(float)Q));
+#pragma unroll
+            for (int e = 0; e < TM * TN; e += 2) {
+                const int i = e / TN, j = e % TN, slot = e % 16;
+                uint64_t pr2, u2, t2, d2, v2;
+                asm("mov.b64 %0, {%1, %1};" : "=l"(pr2) : "f"((float)prs[i / 4][j / 4]));
+                const float u0 = rint_epi((float)acc[i][j]), u1 = rint_epi((float)acc[i][j + 1]);
+                acc[i][j] = T(0);
+                acc[i][j + 1] = T(0);
+                asm("mov.b64 %0, {%1, %2};" : "=l"(u2) : "f"(u0), "f"(u1));       // eq. 9
+                asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t2) : "l"(z2), "l"(u2));
+                float t0, t1;
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(t0), "=f"(t1) : "l"(t2));
+                t0 = rint_epi(t0);
+                t1 = rint_epi(t1);
+                asm("mov.b64 %0, {%1, %2};" : "=l"(t2) : "f"(t0), "f"(t1));
+                asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d2) : "l"(nq2), "l"(t2), "l"(u2));  // eq. 10
+                if (slot == 0) {
+                    if (first) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) v[q] = 0.f;
+                    } else {
+                        tmem_ld16(tcol + (uint32_t)e, v);
+                    }
+                }
+                asm("mov.b64 %0, {%1, %2};" : "=l"(v2) : "f"(v[slot]), "f"(v[slot + 1]));
+                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(v2) : "l"(d2), "l"(pr2));
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(v[slot]), "=f"(v[slot + 1]) : "l"(v2));
+                if (slot == 14) tmem_st16(tcol + (uint32_t)(e - 14), v);
+            }
+            tmem_wait_st();
+            continue;
+        }
 #pragma unroll
         for (int e = 0; e < TM * TN; ++e) {
             const int i = e / TN, j = e % TN;

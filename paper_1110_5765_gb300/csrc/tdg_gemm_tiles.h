@@ -10,9 +10,10 @@ struct Tiles {
     static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, BK = BK_, STAGES = STAGES_;
 };
 
-// fp32 plain / symmetric: 128 x 128 CTA tile, 8 x 8 per thread, 16-k stages x 6
-// (the best of a sweep of k-tile, ring depth and thread tile on GB300)
-using TilesF32 = Tiles<128, 128, 8, 8, 16, 6>;
+// fp32 plain / symmetric: 128 x 128 CTA tile, 8 x 8 per thread, 32-k stages x 3
+// (the best of a sweep of k-tile, ring depth and thread tile on GB300 with the
+// packed f32x2 main loop; 96 KB of ring keeps two CTAs per SM)
+using TilesF32 = Tiles<128, 128, 8, 8, 32, 3>;
 // fp32 asymmetric: 64 packed rows (W result rows each) x 128 columns
 using TilesF32Asym = Tiles<64, 128, 4, 8, 16, 6>;
 // fp64: 64 x 64, 4 x 4 per thread
