@@ -194,6 +194,19 @@ tdg_status tdgemm_quantize_pack(tdgemm_plan_t plan, const void *A, const void *B
                                 void *stream);
 
 /*
+ * Steps (a) and (b) for A alone, reusing B: its statistics, companders and
+ * packed (or copied, or coded) form from the last tdgemm_quantize_pack, whose
+ * B the caller keeps unchanged in place (for a product repeated with a fixed
+ * right operand, e.g. inference with fixed weights).  Valid when B's
+ * companders do not depend on A: fixed-bit and manual plans, the PLAIN and the
+ * TC_FP8 forms; TDG_EINVAL for distortion-target plans (their Gamma_A, Gamma_B
+ * come from both operands), TDG_ESTATE before any tdgemm_quantize_pack or after
+ * tdgemm_set_manual / tdgemm_set_kernel_control.  Non-finite values in B were
+ * reported by the pack that processed B, not again here.
+ */
+tdg_status tdgemm_quantize_pack_a(tdgemm_plan_t plan, const void *A, void *stream);
+
+/*
  * Steps (c) and (d): packed multiply-accumulate with unpacking,
  * de-companding and the sum over slabs fused into the accumulator
  * registers, then C = alpha * C_acc + beta * C (C not read when beta == 0).

@@ -24,6 +24,7 @@ STATUS = {0: "TDG_OK", 1: "TDG_EINVAL", 2: "TDG_ENOMEM", 3: "TDG_ECUDA", 4: "TDG
 # every symbol include/tdgemm.h declares
 EXPORTS = ["tdgemm_plan", "tdgemm_set_rep_noise", "tdgemm_set_manual",
            "tdgemm_set_kernel_control", "tdgemm_kernel_mask", "tdgemm_quantize_pack",
+           "tdgemm_quantize_pack_a",
            "tdgemm_gemm", "tdgemm_run", "tdgemm_run_host", "tdgemm_unpack", "tdgemm_plan_info",
            "tdgemm_plan_destroy", "tdgemm_snr", "tdgemm_run_static", "tdgemm_last_error",
            "tdgemm_version"]
@@ -62,6 +63,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.tdgemm_set_kernel_control.argtypes = [vp, i32, dbl]
     L.tdgemm_kernel_mask.argtypes = [vp, vp, i64]
     L.tdgemm_quantize_pack.argtypes = [vp, vp, vp, vp]
+    L.tdgemm_quantize_pack_a.argtypes = [vp, vp, vp]
     L.tdgemm_gemm.argtypes = [vp, vp, dbl, dbl, vp]
     L.tdgemm_run.argtypes = [vp, vp, vp, vp, dbl, dbl, vp]
     L.tdgemm_run_host.argtypes = [vp, vp, vp, vp, dbl, dbl, vp]

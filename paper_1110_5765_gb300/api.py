@@ -148,9 +148,15 @@ class Plan:
         if X.dtype != want:
             raise ValueError(f"{what} must be {want}")
 
-    def quantize_pack(self, A: torch.Tensor, B: torch.Tensor, stream=None):
-        """A, B: the STORED matrices matching the plan's trans flags and lds."""
+    def quantize_pack(self, A: torch.Tensor, B: torch.Tensor | None = None, stream=None):
+        """A, B: the STORED matrices matching the plan's trans flags and lds.
+        B = None reuses the B of the previous call (fixed-bit, manual, plain
+        and E4M3 plans; the caller keeps that B unchanged)."""
         self._check_operand(A, self.transA, self.lda, "A")
+        if B is None:
+            self._keep = (A, self._keep[1] if getattr(self, "_keep", None) else None)
+            check(self._L.tdgemm_quantize_pack_a(self._h, A.data_ptr(), _stream_ptr(stream)))
+            return
         self._check_operand(B, self.transB, self.ldb, "B")
         self._keep = (A, B)
         check(self._L.tdgemm_quantize_pack(self._h, A.data_ptr(), B.data_ptr(), _stream_ptr(stream)))

@@ -91,7 +91,7 @@ struct tdgemm_plan_s {
     unsigned char *kmask = nullptr;
     // state
     const void *A_user = nullptr, *B_user = nullptr;
-    bool packed = false, gemm_done = false;
+    bool packed = false, gemm_done = false, b_packed = false;
     int last_pack_W = 0;
     cudaStream_t last_stream = nullptr;
     int device = 0;
@@ -291,12 +291,13 @@ extern "C" tdg_status tdgemm_set_manual(tdgemm_plan_t p, int q, double c_a, doub
     p->manual_q = q;
     p->manual_cA = c_a;
     p->manual_cB = c_b;
+    p->b_packed = false;   // B's companders changed
     return TDG_OK;
 }
 
 extern "C" tdg_status tdgemm_set_kernel_control(tdgemm_plan_t p, int mode, double value) {
     if (!p) return fail(TDG_EINVAL, "plan is NULL");
-    if (mode == 0) { p->kctrl_mode = 0; p->packed = false; return TDG_OK; }
+    if (mode == 0) { p->kctrl_mode = 0; p->packed = p->b_packed = false; return TDG_OK; }
     if (p->form != TDG_SYM) return fail(TDG_EINVAL, "inner-kernel control needs the SYM form");
     if (p->mode == MODE_MANUAL) return fail(TDG_EINVAL, "inner-kernel control needs a planned (not manual) plan");
     if (mode != 1 && mode != 2) return fail(TDG_EINVAL, "mode must be 0, 1 (SNR) or 2 (fraction)");
@@ -332,7 +333,7 @@ extern "C" tdg_status tdgemm_set_kernel_control(tdgemm_plan_t p, int mode, doubl
     p->kctrl_value = value;
     p->kctrl_thr = mode == 1 ? pow(10.0, value / 10.0) : 0.0;
     p->kctrl_k = mode == 2 ? (long long)ceil(value * (double)T) : 0;
-    p->packed = false;   // the packed operands no longer match: pack again
+    p->packed = p->b_packed = false;   // the packed operands no longer match: pack again
     return TDG_OK;
 }
 
@@ -382,7 +383,10 @@ static PackOperand<T> operand_B(const tdgemm_plan_s *p, const T *B, const T *c) 
 }
 
 template <typename T>
-static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_t st) {
+static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_t st,
+                            bool reuse_b = false) {
+    // reuse_b: B, its statistics, companders and packed copy are those of the
+    // previous pack (the caller keeps B unchanged); only A is processed
     CU_TRY(cudaMemsetAsync(p->dplan, 0, sizeof(DevPlan), st));
     if (p->stab_dirty) {
         CU_TRY(cudaMemcpyAsync(p->stab, p->stab_host.data(), p->stab_host.size() * 8,
@@ -393,7 +397,7 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
     if (p->form != TDG_PLAIN && p->mode != MODE_MANUAL) {
         // stats of op(A): stored rows x cols; op block grid nM x nK
         CU_TRY(launch_block_stats<T>(A, nA ? p->M : p->K, nA ? p->K : p->M, p->lda, nA ? 0 : 1,
-                                     p->nK, p->mA, p->eA, B, nB ? p->K : p->N,
+                                     p->nK, p->mA, p->eA, B, reuse_b ? 0 : (nB ? p->K : p->N),
                                      nB ? p->N : p->K, p->ldb, nB ? 0 : 1, p->nN, p->mB, p->eB,
                                      p->L, p->dplan, st));
     }
@@ -410,7 +414,7 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
         if (!directA)
             CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, nullptr), 1, p->dplan, 0, 0, (T *)p->kA,
                                     s0.a_ld, s0.a_rows, st));
-        if (!directB)
+        if (!directB && !reuse_b)
             CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, nullptr), 1, p->dplan, 0, 0, (T *)p->kB,
                                     s0.b_ld, s0.b_rows, st));
     }
@@ -419,7 +423,9 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
             const long long ldk = round_up(p->K, 128);
             const int fp8 = p->form == TDG_TC_FP8;
             CU_TRY(launch_codes(operand_A<float>(p, A, (const float *)p->cA), fp8, p->Abuf, ldk, st));
-            CU_TRY(launch_codes(operand_B<float>(p, B, (const float *)p->cB), fp8, p->Bbuf, ldk, st));
+            if (!reuse_b)
+                CU_TRY(launch_codes(operand_B<float>(p, B, (const float *)p->cB), fp8, p->Bbuf, ldk,
+                                    st));
         }
     } else {
         for (int w : candidates(p)) {
@@ -433,19 +439,21 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
                 if (!directA)
                     CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, nullptr), 1, p->dplan, 1, 0,
                                             (T *)p->Abuf, s.a_ld, s.a_rows, st));
-                if (!directB)
+                if (!directB && !reuse_b)
                     CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, nullptr), 1, p->dplan, 1, 0,
                                             (T *)p->Bbuf, s.b_ld, s.b_rows, st));
             } else if (p->form == TDG_SYM) {
                 CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w, -1,
                                         (T *)p->Abuf, s.a_ld, s.a_rows, st));                   // eq. 6
-                CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, (const T *)p->cB), w, p->dplan, w, +1,
-                                        (T *)p->Bbuf, s.b_ld, s.b_rows, st));                   // eq. 7
+                if (!reuse_b)
+                    CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, (const T *)p->cB), w, p->dplan, w,
+                                            +1, (T *)p->Bbuf, s.b_ld, s.b_rows, st));      // eq. 7
             } else {
                 CU_TRY(launch_pack_x<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w, -1,
                                         (T *)p->Abuf, s.a_ld, st));                   // eq. 11
-                CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, (const T *)p->cB), 1, p->dplan, w, 0,
-                                        (T *)p->Bbuf, s.b_ld, s.b_rows, st));                   // b~ only
+                if (!reuse_b)
+                    CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, (const T *)p->cB), 1, p->dplan, w,
+                                            0, (T *)p->Bbuf, s.b_ld, s.b_rows, st));       // b~ only
             }
         }
     }
@@ -462,8 +470,27 @@ extern "C" tdg_status tdgemm_quantize_pack(tdgemm_plan_t p, const void *A, const
     if (!p) return fail(TDG_EINVAL, "plan is NULL");
     if (!A || !B) return fail(TDG_EINVAL, "A and B must be device pointers");
     cudaStream_t st = (cudaStream_t)stream;
-    if (p->dtype == TDG_F64) return pack_impl<double>(p, (const double *)A, (const double *)B, st);
-    return pack_impl<float>(p, (const float *)A, (const float *)B, st);
+    tdg_status r = p->dtype == TDG_F64
+                       ? pack_impl<double>(p, (const double *)A, (const double *)B, st)
+                       : pack_impl<float>(p, (const float *)A, (const float *)B, st);
+    if (r == TDG_OK) p->b_packed = true;
+    return r;
+}
+
+extern "C" tdg_status tdgemm_quantize_pack_a(tdgemm_plan_t p, const void *A, void *stream) {
+    if (!p) return fail(TDG_EINVAL, "plan is NULL");
+    if (!A) return fail(TDG_EINVAL, "A must be a device pointer");
+    if (!(p->mode == MODE_FIXED || p->mode == MODE_MANUAL || p->form == TDG_PLAIN ||
+          p->form == TDG_TC_FP8))
+        return fail(TDG_EINVAL,
+                    "B can be reused only when its companders do not depend on A (fixed bits, "
+                    "manual parameters, the plain or the E4M3 form)");
+    if (!p->b_packed || !p->B_user)
+        return fail(TDG_ESTATE, "tdgemm_quantize_pack_a before a tdgemm_quantize_pack with B");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->dtype == TDG_F64)
+        return pack_impl<double>(p, (const double *)A, (const double *)p->B_user, st, true);
+    return pack_impl<float>(p, (const float *)A, (const float *)p->B_user, st, true);
 }
 
 template <typename T>

@@ -138,6 +138,32 @@ def test_target_mode_with_control_and_epilogue(tdg, orc, rms):
     assert same_bits(C, ref.C)
 
 
+@pytest.mark.parametrize("trans", ["NT", "TN", "TT"])
+def test_transposed_operands(tdg, orc, trans):
+    """Stored transposes: the conventional-product tiles read op(A) / op(B)
+    from the caller's buffers where the layout allows (A stored 'T', B stored
+    'N') and from the plan's copies otherwise; mask and C unchanged."""
+    tA, tB = trans[0], trans[1]
+    dtype, L = "f32", 128
+    A, B = inputs((384, 256, 300), L, dtype, 970)
+    M, K = A.shape
+    N = B.shape[1]
+    As = np.ascontiguousarray(A.T) if tA == "T" else A
+    Bs = np.ascontiguousarray(B.T) if tB == "T" else B
+    ref = orc.tdgemm(A, B, L=L, W=2, dtype=dtype, form="sym", bits=6,
+                     kernel_control=("fraction", 0.4))
+    p = tdg.Plan(M, N, K, L=L, W=2, dtype=dtype, form="sym", bits=6, rep_noise=None,
+                 transA=tA, transB=tB)
+    p.set_kernel_control("fraction", 0.4)
+    C = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    p.run(dev(As), dev(Bs), C)
+    torch.cuda.synchronize()
+    assert p.info()["device_status"] == 0
+    assert np.array_equal(p.kernel_mask().astype(bool), ref.plan.extra["kernel_mask"])
+    assert same_bits(C.cpu().numpy(), ref.C)
+    p.close()
+
+
 def test_fallback_plan_accelerates_nothing(tdg, orc):
     """A target no packing can meet: the planner falls back to W = 1, the mask
     is empty and C is the conventional product."""
