@@ -540,6 +540,104 @@ def kernel_control_sweep(out_path=None):
     return recs
 
 
+def pca2d_study(out_path=None):
+    """Sec. 8.A's 2DPCA face recognition with every GEMM through the library
+    (Table 1's rows): synthetic faces (15 persons x 11 images of 288 x 288,
+    5 training and 6 test images each, d = 10), G = sum_j A_j A_j^T as one
+    288 x 288 x 21600 GEMM, the projections of all 165 images as 21600 x 288 x 10
+    and 25920 x 288 x 10 GEMMs.  For each method: recognition rate, W the
+    planner chose per GEMM, SNR of each GEMM against fp64, and effective
+    GFLOP/s over the three GEMMs (device-resident operands, CUDA events, mean of
+    five runs after one warm-up).  These sizes fill only part of a GB300 (the G
+    product has 9 output tiles of 128 x 128)."""
+    import torch
+    from paper_1110_5765_gb300 import build as b
+    b.build()
+    import paper_1110_5765_gb300 as tdg
+    torch.backends.cuda.matmul.allow_tf32 = False
+    faces = synth.faces_2dpca(15, 11, 288, 7)
+    n, d, n_train = 288, 10, 5
+    train = faces[:, :n_train].reshape(-1, n, n)
+    test = faces[:, n_train:].reshape(-1, n, n)
+    mean = train.mean(axis=0)
+    tr = (train - mean).astype(np.float32)
+    te = (test - mean).astype(np.float32)
+    side = np.ascontiguousarray(np.concatenate(list(tr), axis=1))
+    truth = np.repeat(np.arange(15), 6)
+
+    def study(make):
+        """make(M, N, K) -> callable(A, B) -> C on the device"""
+        t_total, info = 0.0, {}
+        flops = 0.0
+
+        def mm(A, B, name):
+            nonlocal t_total, flops
+            M, K = A.shape
+            N = B.shape[1]
+            fn = make(M, N, K)
+            dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+            dB = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+            C, extra = fn(dA, dB)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                C, extra = fn(dA, dB)
+            e1.record()
+            torch.cuda.synchronize()
+            t_total += e0.elapsed_time(e1) / 1e3 / 5
+            flops += 2.0 * M * N * K
+            Cn = C.float().cpu().numpy()
+            ref = A.astype(np.float64) @ B.astype(np.float64)
+            err = np.sum((Cn - ref) ** 2)
+            info[name] = dict(extra, snr_db=(math.inf if err == 0 else
+                                             10 * math.log10(np.sum(ref ** 2) / err)))
+            return Cn
+
+        G = mm(side, np.ascontiguousarray(side.T), "G")
+        w, V = np.linalg.eigh(G.astype(np.float64))
+        X = np.ascontiguousarray(V[:, ::-1][:, :d]).astype(np.float32)
+        Ytr = mm(np.ascontiguousarray(tr.reshape(-1, n)), X, "Ytrain").reshape(len(tr), n, d)
+        Yte = mm(np.ascontiguousarray(te.reshape(-1, n)), X, "Ytest").reshape(len(te), n, d)
+        dist = ((Yte[:, None].astype(np.float64) - Ytr[None]) ** 2).sum(axis=(2, 3))
+        acc = float(((dist.argmin(axis=1) // n_train) == truth).mean())
+        return {"recognition": acc, "gflops": flops / t_total / 1e9, "ms": t_total * 1e3,
+                "gemms": info}
+
+    def cublas(M, N, K):
+        return lambda A, B: (torch.matmul(A, B), {})
+
+    def plan_maker(**kw):
+        manual = kw.pop("manual", None)
+
+        def make(M, N, K):
+            p = tdg.Plan(M, N, K, L=L_BLOCK, dtype="f32", **kw)
+            if manual:
+                p.set_manual(*manual)
+
+            def fn(A, B):
+                C = p.run(A, B)
+                i = p.info()
+                return C, {"W_used": i["W_used"], "pred_snr_db": i["pred_snr_db"]}
+            return fn
+        return make
+
+    recs = {}
+    recs["cuBLAS fp32"] = study(cublas)
+    recs["plain fp32"] = study(plan_maker(W=1, form="plain"))
+    recs["50 dB"] = study(plan_maker(W=2, form="sym", target_snr_db=50.0, noise_rms=True))
+    recs["20 dB"] = study(plan_maker(W=2, form="sym", target_snr_db=20.0, noise_rms=True))
+    q = (2 * 50000 + 50 - 1).bit_length()      # eq. 15 for R_max = 50000
+    recs["ad-hoc (W = 2, R_max = 50000, c = 0.1)"] = study(
+        plan_maker(W=2, form="sym", bits=8, manual=(q, 0.1, 0.1)))
+    for k, v in recs.items():
+        print(json.dumps({"method": k, **v}), flush=True)
+    if out_path:
+        with open(out_path, "w") as f:
+            json.dump(recs, f)
+    return recs
+
+
 def measure_precision_form(tdg, torch) -> dict:
     """The precision-form workload: 8192^3 Laplacian(b = 1) fp32, L = 128,
     tensor-core forms and the packed CUDA-core forms at a 40 dB target, beside
@@ -597,11 +695,16 @@ def main():
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--sweep", default=None, metavar="OUT.json",
                     help="run the 4096^3 distortion sweep (168 runs) and write its records")
+    ap.add_argument("--pca2d", default=None, metavar="OUT.json",
+                    help="run the 2DPCA face-recognition study (Sec. 8.A, Table 1)")
     ap.add_argument("--fig7", default=None, metavar="OUT.json",
                     help="run the 4096^3 inner-kernel throughput-control sweep (Sec. 6)")
     args = ap.parse_args()
     if args.fig7:
         kernel_control_sweep(args.fig7)
+        return
+    if args.pca2d:
+        pca2d_study(args.pca2d)
         return
     if args.sweep:
         sweep(args.sweep)

@@ -92,6 +92,7 @@ struct tdgemm_plan_s {
     // state
     const void *A_user = nullptr, *B_user = nullptr;
     bool packed = false, gemm_done = false, b_packed = false;
+    int split_groups = 1;   // slab splitting of the packed GEMM (> 1: on)
     int last_pack_W = 0;
     cudaStream_t last_stream = nullptr;
     int device = 0;
@@ -227,15 +228,33 @@ extern "C" tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB,
         abytes = (size_t)M * ldk * e1;
         bbytes = (size_t)N * ldk * e1;
     } else {
+        // slab splitting for few output tiles over many slabs (e.g. 288 x 288 x
+        // 21600): the packed slab products of a tile run on several CTAs and
+        // the ordered sum over slabs in the unpack kernel; needs the r-bar
+        // buffer that TDG_KEEP_PACKED also uses
+        if (is_packed_form(form) && !(flags & TDG_KEEP_PACKED) && p->nK >= 4) {
+            int bxa, bxb, bk, dev = 0, sms = 0;
+            packed_gemm_boxes(dtype, form == TDG_SYM ? G_SYM : G_ASYM, &bxa, &bxb, &bk);
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const long long mrows = form == TDG_ASYM ? (long long)p->nM * Pof(L, W) : M;
+            const long long ntiles = ((mrows + bxa - 1) / bxa) * ((N + bxb - 1) / bxb);
+            if (sms > 0 && ntiles * 2 <= sms)
+                p->split_groups = (int)std::min<long long>(p->nK, (2LL * sms + ntiles - 1) / ntiles);
+        }
         for (int w : candidates(p)) {
             OpShape s = op_shape(p, w);
             abytes = std::max(abytes, (size_t)(s.a_rows * s.a_ld) * p->esz);
             bbytes = std::max(bbytes, (size_t)(s.b_rows * s.b_ld) * p->esz);
-            if ((flags & TDG_KEEP_PACKED) && w >= 1 && is_packed_form(form)) {
+            if ((flags & TDG_KEEP_PACKED || p->split_groups > 1) && w >= 1 && is_packed_form(form)) {
                 long long mrows = form == TDG_ASYM ? (long long)p->nM * Pof(L, w) : M;
                 rbytes = std::max(rbytes, (size_t)((size_t)p->nK * (size_t)mrows * (size_t)N * p->esz));
             }
         }
+    }
+    if (p->split_groups > 1 && !(flags & TDG_KEEP_PACKED) && rbytes > ((size_t)1 << 30)) {
+        p->split_groups = 1;       // the r-bar buffer would exceed 1 GiB
+        rbytes = 0;
     }
     size_t o_A = off; off += up(abytes);
     size_t o_B = off; off += up(bbytes);
@@ -531,6 +550,11 @@ static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cu
         g.C = C; g.ldc = p->ldc;
         g.alpha = (T)alpha; g.beta = (T)beta; g.beta_zero = beta == 0.0;
         g.Rbar = (!plain && (p->flags & TDG_KEEP_PACKED)) ? (T *)p->Rbar : nullptr;
+        const bool split = !plain && p->split_groups > 1 && !p->kctrl_mode && p->Rbar;
+        if (split) {
+            g.Rbar = (T *)p->Rbar;
+            g.groups = p->split_groups;
+        }
         if (p->kctrl_mode && !plain) {
             // Sec. 6: the tiles of inner kernels left unaccelerated compute the
             // conventional product from the plain operands, same launch
@@ -542,6 +566,7 @@ static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cu
             return fail(TDG_ECUDA, "packed GEMM: an operand could not be mapped for TMA");
         if (e != cudaSuccess)
             return fail(TDG_ECUDA, "packed GEMM launch failed: %s", cudaGetErrorString(e));
+        if (split) CU_TRY(launch_unpack<T>(gform, Wk, g, nullptr, st));   // sum over slabs, C
     }
     return TDG_OK;
 }
@@ -634,6 +659,7 @@ extern "C" tdg_status tdgemm_unpack(tdgemm_plan_t p, int64_t *rint_out, void *C,
         g.Krows = s.a_rows; g.L = p->L; g.P = Pof(p->L, w); g.nM = p->nM; g.nK = p->nK;
         g.nN = p->nN; g.pair = (const double *)p->pair; g.C = (double *)C; g.ldc = p->ldc;
         g.Rbar = (double *)p->Rbar;
+        g.alpha = 1.0; g.beta_zero = 1;           // C = sum over slabs, as it stands
         CU_TRY(launch_unpack<double>(gform, w, g, rint_out, st));
     } else {
         GemmArgs<float> g{};
@@ -641,6 +667,7 @@ extern "C" tdg_status tdgemm_unpack(tdgemm_plan_t p, int64_t *rint_out, void *C,
         g.Krows = s.a_rows; g.L = p->L; g.P = Pof(p->L, w); g.nM = p->nM; g.nK = p->nK;
         g.nN = p->nN; g.pair = (const float *)p->pair; g.C = (float *)C; g.ldc = p->ldc;
         g.Rbar = (float *)p->Rbar;
+        g.alpha = 1.0f; g.beta_zero = 1;          // C = sum over slabs, as it stands
         CU_TRY(launch_unpack<float>(gform, w, g, rint_out, st));
     }
     return TDG_OK;

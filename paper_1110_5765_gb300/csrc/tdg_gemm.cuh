@@ -228,10 +228,14 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
 
     // the device planner chose another packing
     if (g.plan->W != W) return;
-    // this CTA's tile, row-major over ntn tiles per row
-    const long long tmi = (long long)(blockIdx.x / g.ntn);
+    // this CTA's tile, row-major over ntn tiles per row; with slab splitting
+    // (KEEP instantiation, groups > 1) CTA b takes tile b % ntiles and the
+    // slabs of group b / ntiles
+    const bool split = KEEP && g.groups > 1;
+    const long long tix = split ? (long long)blockIdx.x % g.ntiles : (long long)blockIdx.x;
+    const long long tmi = tix / g.ntn;
     const long long x0 = tmi * BM;                      // first A-operand column (m or packed row)
-    const long long n0 = ((long long)blockIdx.x - tmi * g.ntn) * BN;
+    const long long n0 = (tix - tmi * g.ntn) * BN;
     bool plain_tile = false;
     if constexpr (MIX) plain_tile = g.kmask[(x0 / g.L) * g.nN + n0 / g.L] == 0;
     const CUtensorMap *mA = plain_tile ? &mapPA : &mapA;
@@ -247,12 +251,14 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
     const int warp = tid >> 5;
     const SlabWalk<T, FORM> walk{g};
     const SlabWalk<T, G_PLAIN> pwalk{g};
-    const int nslab = plain_tile ? 1 : walk.nslab();
+    const int nslab_all = plain_tile ? 1 : walk.nslab();
+    const int l_begin = split ? (int)((long long)blockIdx.x / g.ntiles) * g.spg : 0;
+    const int nslab = split ? min(nslab_all, l_begin + g.spg) : nslab_all;   // end of this CTA's slabs
     auto slab_len = [&](int l) { return plain_tile ? pwalk.len(l) : walk.len(l); };
     auto slab_row0 = [&](int l) { return plain_tile ? 0LL : walk.row0(l); };
 
     // ---- loads: thread 0 keeps STAGES - 1 tiles in flight ahead of the math
-    int pl = 0, ps = 0, issued = 0;    // next tile to load: slab pl, stage ps
+    int pl = l_begin, ps = 0, issued = 0;    // next tile to load: slab pl, stage ps
     auto issue_next = [&]() {
         if (pl >= nslab) return;
         const int stage = issued % STAGES;
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
 
     int it = 0;
     bool ok = true;
-    for (int l = 0; l < nslab && ok; ++l) {
+    for (int l = l_begin; l < nslab && ok; ++l) {
         const int slen = slab_len(l);
         for (int s = 0; s * BK < slen; ++s, ++it) {
             const int stage = it % STAGES;
@@ -400,6 +406,24 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
             for (int hj = 0; hj < CG; ++hj)
                 prs[pi][hj] = __ldg(pl_tab + (long long)iblk[FORM == G_ASYM ? pi : 4 * pi] * g.nN + jblk[hj]);
         float v[16];
+        if constexpr (KEEP) {
+            if (split) {
+                // slab splitting: only the packed slab results leave the CTA;
+                // the ordered sum over slabs runs in the unpack kernel
+#pragma unroll
+                for (int i = 0; i < TM; ++i) {
+                    const long long xr = x0 + (i / 4) * (BM / RG) + ty * 4 + (i % 4);
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) {
+                        const long long nc = out_col(j);
+                        if (xr < g.Mrows && nc < g.N)
+                            g.Rbar[((long long)l * g.Mrows + xr) * g.N + nc] = acc[i][j];
+                        acc[i][j] = T(0);
+                    }
+                }
+                continue;
+            }
+        }
         if constexpr (FORM == G_SYM && TMEMC && !KEEP && TN % 2 == 0) {
             // eqs. 9-10 and the fma into the running sum on adjacent column
             // pairs (same factor, adjacent TMEM columns): the products and
@@ -490,6 +514,8 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         // let every copy this CTA issued land before it exits
         if (tid == 0)
             for (int k = it; k < issued; ++k) mbar_wait_bounded(&full[k % STAGES], (k / STAGES) & 1);
+    } else if (split) {
+        // C is written by the unpack kernel
     } else if (MIX && plain_tile) {
         // ------------------------------------------------------------ store C
         // of a conventional-product tile, straight from the fma chains
@@ -564,8 +590,19 @@ cudaError_t launch_grid(const GemmArgs<T> &g0, const GemmOperands &ops, cudaStre
     GemmArgs<T> g = g0;
     g.ntn = (int)((g.N + C::BN - 1) / C::BN);
     const long long ntiles = ((g.Mrows + C::BM - 1) / C::BM) * g.ntn;
-    if (ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)ntiles, Cfg::NT, Cfg::SMEM, st>>>(ma, mb, mpa, mpb, g);
+    g.ntiles = ntiles;
+    long long nblocks = ntiles;
+    if (KEEP && g.groups > 1) {
+        // slab splitting: groups of spg consecutive slabs per CTA
+        const int nsl = FORM == G_PLAIN ? 1 : g.nK;
+        g.spg = (nsl + g.groups - 1) / g.groups;
+        g.groups = (nsl + g.spg - 1) / g.spg;
+        nblocks = ntiles * g.groups;
+    } else {
+        g.groups = 1;
+    }
+    if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    kern<<<(unsigned)nblocks, Cfg::NT, Cfg::SMEM, st>>>(ma, mb, mpa, mpb, g);
     return cudaGetLastError();
 }
 
@@ -582,6 +619,7 @@ cudaError_t launch_cfg(const GemmArgs<T> &g, const GemmOperands &ops, cudaStream
     }
     if (g.kmask) return cudaErrorInvalidValue;
     if (FORM != G_PLAIN && g.Rbar) return launch_grid<T, FORM, W, C, true, false>(g, ops, st);
+    if (g.groups > 1) return cudaErrorInvalidValue;     // slab splitting stores r-bar
     return launch_grid<T, FORM, W, C, false, false>(g, ops, st);
 }
 

@@ -87,6 +87,11 @@ struct GemmArgs {
     // the plain operands in the same launch.
     const unsigned char *kmask;
     int ntn;                // set by the launcher: tiles per row of the 1-D tile grid
+    long long ntiles;       // set by the launcher: tiles in the grid
+    // slab splitting (needs Rbar): > 1 asks for that many groups of slabs, each
+    // CTA computing one tile over one group and storing its packed slab
+    // results; the launcher sets spg (slabs per group) and the final count
+    int groups, spg;
 };
 
 // 2-D TMA map over a row-major [rows][cols] array with leading dimension ld

@@ -4,7 +4,10 @@
 // (TDG_KEEP_PACKED).  This kernel unpacks them exactly as the fused epilogue
 // does — eqs. 9-10 (symmetric) or 13-14 (asymmetric) — and exposes the
 // integers r~ per output and slab (int64), plus C = sum_l r~ (s_A s_B)
-// (eqs. 5, 2), so the integer domain can be compared bit for bit.
+// (eqs. 5, 2), so the integer domain can be compared bit for bit.  It also
+// finishes a slab-split GEMM (few output tiles, many slabs: the slabs' packed
+// products run in parallel and this kernel takes the sum over slabs in their
+// order), then with alpha and beta as the fused epilogue applies them.
 //
 // tdgemm_snr: fp64 sums of ref^2, (C - ref)^2 and (C - ref) for eq. 20.
 #include "tdg_common.cuh"
@@ -22,6 +25,7 @@ __device__ inline T rint_d(T v) {
 
 template <typename T, int ASYM>
 __global__ void unpack_kernel(GemmArgs<T> g, int W, int64_t *rint_out) {
+    if (g.plan->W != W) return;            // the planner chose another packing
     const long long total = g.M * g.N;
     const int q = g.plan->q;
     const T z = sizeof(T) == 4 ? (T)scalbnf(1.0f, -q) : (T)scalbn(1.0, -q);
@@ -67,7 +71,14 @@ __global__ void unpack_kernel(GemmArgs<T> g, int W, int64_t *rint_out) {
             else c = __fma_rn(rt, pr, c);
             if (rint_out) rint_out[e * g.nK + l] = (int64_t)rt;
         }
-        if (g.C) g.C[m * g.ldc + n] = c;
+        if (g.C) {
+            // the GEMM epilogue: C = alpha c (beta == 0) or alpha c + beta C
+            T *pc = g.C + m * g.ldc + n;
+            if constexpr (sizeof(T) == 4)
+                *pc = g.beta_zero ? __fmul_rn(g.alpha, c) : __fmaf_rn(g.alpha, c, __fmul_rn(g.beta, *pc));
+            else
+                *pc = g.beta_zero ? __dmul_rn(g.alpha, c) : __fma_rn(g.alpha, c, __dmul_rn(g.beta, *pc));
+        }
     }
 }
 

@@ -31,6 +31,7 @@ __all__ = [
     "blockwise_range_uniform",
     "blockwise_crest",
     "eigenface_pixels",
+    "faces_2dpca",
     "mlp_teacher",
     "mlp_inputs",
     "sample_tiles",
@@ -114,6 +115,42 @@ def eigenface_pixels(pixels: int, images: int, seed: int, dtype=np.float32) -> n
     x = rng(seed).integers(0, 256, size=(pixels, images)).astype(np.float64)
     x -= x.mean(axis=1, keepdims=True)
     return _cast(x, dtype)
+
+
+def faces_2dpca(persons: int, per_person: int, size: int, seed: int,
+                person_amp: float = 13.0, image_amp: float = 16.0,
+                noise: float = 20.0) -> np.ndarray:
+    """Synthetic face images for the 2DPCA recognition study, shape
+    (persons, per_person, size, size), integer pixel values 0..255.
+
+    Every image is 128 + gain * (common + person_p) + variation + noise: a
+    component shared by all persons and one per person, each a sum of random
+    low-frequency 2-D cosines (amplitudes ~ N(0, 40^2) and ~ N(0, person_amp^2)
+    per mode), an image gain from U[0.8, 1.2], an image-specific cosine field
+    (~ N(0, image_amp^2) per mode) and pixel noise N(0, noise^2), clipped and
+    rounded.  The defaults give a nearest-neighbour recognition rate near the
+    paper's 78 % with 5 training and 6 test images per person and d = 10."""
+    g = rng(seed)
+    yy, xx = np.mgrid[0:size, 0:size] / float(size)
+
+    def field(nmodes: int, amp: float) -> np.ndarray:
+        f = np.zeros((size, size))
+        for _ in range(nmodes):
+            fx, fy = g.uniform(0.5, 6.0, 2)
+            ph = g.uniform(0.0, 2.0 * np.pi, 2)
+            a = g.normal() * amp
+            f += a * np.cos(2 * np.pi * fx * xx + ph[0]) * np.cos(2 * np.pi * fy * yy + ph[1])
+        return f
+
+    common = field(16, 40.0)
+    out = np.empty((persons, per_person, size, size))
+    for p in range(persons):
+        base = common + field(8, person_amp)
+        for k in range(per_person):
+            gain = g.uniform(0.8, 1.2)
+            im = 128.0 + gain * base + field(16, image_amp) + g.normal(0.0, noise, (size, size))
+            out[p, k] = np.clip(np.rint(im), 0, 255)
+    return out
 
 
 def mlp_teacher(sizes, seed: int, dtype=np.float32):

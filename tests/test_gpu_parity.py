@@ -284,3 +284,22 @@ def test_fixed_bits_per_block_companders(tdg, orc, dtype, form, W):
     ref = orc.tdgemm(A, B, L=64, W=W, dtype=dtype, form=form, bits=6)
     g = run_gpu(tdg, A, B, L=64, W=W, dtype=dtype, form=form, bits=6)
     assert same_bits(g["C"], ref.C)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("form", ["sym", "asym"])
+def test_few_tiles_many_slabs(tdg, orc, dtype, form):
+    """Few output tiles over many slabs (the plan splits the slabs of each tile
+    over several CTAs and sums them in order in a second kernel): C equals the
+    oracle bit for bit, including alpha / beta, beyond the error-free region."""
+    T = NP[dtype]
+    M, K, N = 200, 4096 + 70, 250
+    A = synth.laplace((M, K), 1301, T)
+    B = synth.gaussian((K, N), 1302, T)
+    Cin = synth.gaussian((M, N), 1303, T)
+    W = 2 if dtype == "f32" else 3
+    ref = orc.tdgemm(A, B, L=128, W=W, dtype=dtype, form=form, bits=7, alpha=0.75, beta=-1.5,
+                     C_in=Cin)
+    g = run_gpu(tdg, A, B, L=128, W=W, dtype=dtype, form=form, bits=7, alpha=0.75, beta=-1.5,
+                Cin=Cin)
+    assert same_bits(g["C"], ref.C)

@@ -108,3 +108,79 @@ def test_distortion_sweep_points(tdg, orc, dtype, kind):
                     snr = tdg.snr_db(C, ref_full)
                     tol = 1.0 if info["W_used"] <= info["w_ef"] else 3.0
                     assert snr > info["pred_snr_db"] - tol, (form, W, target, snr, info)
+
+
+# ------------------------------------------------------------------ 2DPCA recognition (Sec. 8.A)
+def _2dpca(faces, matmul, d=10, n_train=5):
+    """Sec. 8.A: G = sum_j A_j A_j^T over the mean-removed training images (one
+    GEMM with the images side by side), X = the d leading eigenvectors of G,
+    Y = A X for every image (one GEMM with the images stacked), and each test
+    image takes the person of the training image nearest in Frobenius norm."""
+    persons, per, n, _ = faces.shape
+    train = faces[:, :n_train].reshape(-1, n, n)
+    test = faces[:, n_train:].reshape(-1, n, n)
+    mean = train.mean(axis=0)
+    tr = (train - mean).astype(np.float32)
+    te = (test - mean).astype(np.float32)
+    side = np.ascontiguousarray(np.concatenate(list(tr), axis=1))      # n x (J n)
+    G = matmul(side, np.ascontiguousarray(side.T), "G")
+    w, V = np.linalg.eigh(G.astype(np.float64))
+    X = np.ascontiguousarray(V[:, ::-1][:, :d]).astype(np.float32)
+    Ytr = matmul(np.ascontiguousarray(tr.reshape(-1, n)), X, "Ytrain").reshape(len(tr), n, d)
+    Yte = matmul(np.ascontiguousarray(te.reshape(-1, n)), X, "Ytest").reshape(len(te), n, d)
+    dist = ((Yte[:, None].astype(np.float64) - Ytr[None]) ** 2).sum(axis=(2, 3))
+    pred = dist.argmin(axis=1) // n_train
+    truth = np.repeat(np.arange(persons), per - n_train)
+    return float((pred == truth).mean()), G
+
+
+@pytest.fixture(scope="module")
+def faces2d():
+    # 15 persons x 11 images of 288 x 288 pixels (the study's split: 5 train, 6 test)
+    return synth.faces_2dpca(15, 11, 288, 7)
+
+
+def test_2dpca_recognition_at_20db(tdg, orc, faces2d):
+    """Every GEMM of the study at a 20 dB target (RMS-scaled representation
+    noise): the planner packs all three at W = 2, recognition stays within two
+    test images of the exact fp64 pipeline, and G is bit-identical to the
+    oracle's; the paper's ad-hoc parameters (W = 2, R_max = 50000, c = 0.1)
+    wreck it (P:451's 44 %)."""
+    acc_exact, _ = _2dpca(faces2d, lambda a, b, _: a.astype(np.float64) @ b.astype(np.float64))
+    plans = {}
+
+    def packed(a, b, name):
+        M, K = a.shape
+        N = b.shape[1]
+        p = tdg.Plan(M, N, K, L=128, W=2, dtype="f32", form="sym", target_snr_db=20.0,
+                     noise_rms=True)
+        C = p.run(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
+        torch.cuda.synchronize()
+        plans[name] = p.info()
+        p.close()
+        return C.cpu().numpy()
+
+    acc20, G20 = _2dpca(faces2d, packed)
+    assert all(i["W_used"] == 2 and i["device_status"] == 0 for i in plans.values()), plans
+    assert abs(acc20 - acc_exact) <= 2 / 90 + 1e-12, (acc20, acc_exact)
+    train = faces2d[:, :5].reshape(-1, 288, 288)
+    tr = (train - train.mean(axis=0)).astype(np.float32)
+    side = np.ascontiguousarray(np.concatenate(list(tr), axis=1))
+    ref = orc.tdgemm(side, np.ascontiguousarray(side.T), L=128, W=2, dtype="f32", form="sym",
+                     target_db=20.0, s_table=orc.load_s_table(), noise_rms=True)
+    assert same_bits(G20, ref.C)
+
+    q = orc.q_for(50000)
+
+    def adhoc(a, b, name):
+        M, K = a.shape
+        N = b.shape[1]
+        p = tdg.Plan(M, N, K, L=128, W=2, dtype="f32", form="sym", bits=8)
+        p.set_manual(q, 0.1, 0.1)
+        C = p.run(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
+        torch.cuda.synchronize()
+        p.close()
+        return C.cpu().numpy()
+
+    acc_adhoc, _ = _2dpca(faces2d, adhoc)
+    assert acc_adhoc < acc_exact - 0.3, (acc_adhoc, acc_exact)
