@@ -638,6 +638,68 @@ def pca2d_study(out_path=None):
     return recs
 
 
+def mlp_study(out_path=None, steps=50):
+    """Config 4, the differentiation form: a 128-1024-1024-10 tanh MLP, batch
+    4096, synthetic labels from a teacher MLP, cross-entropy, SGD lr 0.1.  Every
+    GEMM (3 forward, 5 adjoint products per step) through the straight-through
+    autograd form at a 20 dB target (RMS-scaled noise), beside the same
+    training with torch fp32 matmuls (TF32 off).  Reports ms per step (CUDA
+    events over the steps after two warm-up steps), the loss after `steps`
+    steps, and the W the planner chose for each product."""
+    import torch
+    from paper_1110_5765_gb300 import build as b
+    b.build()
+    from paper_1110_5765_gb300 import autograd as ag
+    torch.backends.cuda.matmul.allow_tf32 = False
+    sizes = [128, 1024, 1024, 10]
+    teacher = [torch.from_numpy(w).cuda() for w in synth.mlp_teacher(sizes, 4)]
+    X = torch.from_numpy(synth.mlp_inputs(4096, 128, 5)).cuda()
+    with torch.no_grad():
+        h = X
+        for k, w in enumerate(teacher):
+            h = h @ w
+            if k < 2:
+                h = torch.tanh(h)
+        labels = h.argmax(1)
+    init = [torch.from_numpy(w).cuda() for w in synth.mlp_teacher(sizes, 6)]
+    opts = dict(L=L_BLOCK, W=2, form="sym", target_snr_db=20.0, noise_rms=True)
+
+    def train(use_tdg):
+        ws = [w.clone().requires_grad_() for w in init]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        loss = None
+        for it in range(steps + 2):
+            if it == 2:
+                torch.cuda.synchronize()
+                e0.record()
+            h = X
+            for k, w in enumerate(ws):
+                h = ag.tdg_matmul(h, w, **opts) if use_tdg else h @ w
+                if k < 2:
+                    h = torch.tanh(h)
+            loss = torch.nn.functional.cross_entropy(h, labels)
+            for w in ws:
+                w.grad = None
+            loss.backward()
+            with torch.no_grad():
+                for w in ws:
+                    w -= 0.1 * w.grad
+        e1.record()
+        torch.cuda.synchronize()
+        return {"ms_per_step": e0.elapsed_time(e1) / steps, "loss": float(loss.detach())}
+
+    ag.clear_plan_cache()
+    out = {"torch fp32": train(False), "tdgemm 20 dB": train(True)}
+    out["tdgemm 20 dB"]["products"] = {
+        f"{k[0]}x{k[1]}x{k[2]} {k[3]}{k[4]}": p.info()["W_used"] for k, p in ag._plans.items()}
+    ag.clear_plan_cache()
+    print(json.dumps(out), flush=True)
+    if out_path:
+        with open(out_path, "w") as f:
+            json.dump(out, f)
+    return out
+
+
 def measure_precision_form(tdg, torch) -> dict:
     """The precision-form workload: 8192^3 Laplacian(b = 1) fp32, L = 128,
     tensor-core forms and the packed CUDA-core forms at a 40 dB target, beside
@@ -695,6 +757,8 @@ def main():
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--sweep", default=None, metavar="OUT.json",
                     help="run the 4096^3 distortion sweep (168 runs) and write its records")
+    ap.add_argument("--mlp", default=None, metavar="OUT.json",
+                    help="time MLP training through the autograd form (config 4)")
     ap.add_argument("--pca2d", default=None, metavar="OUT.json",
                     help="run the 2DPCA face-recognition study (Sec. 8.A, Table 1)")
     ap.add_argument("--fig7", default=None, metavar="OUT.json",
@@ -705,6 +769,9 @@ def main():
         return
     if args.pca2d:
         pca2d_study(args.pca2d)
+        return
+    if args.mlp:
+        mlp_study(args.mlp)
         return
     if args.sweep:
         sweep(args.sweep)
