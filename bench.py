@@ -688,8 +688,53 @@ def mlp_study(out_path=None, steps=50):
         torch.cuda.synchronize()
         return {"ms_per_step": e0.elapsed_time(e1) / steps, "loss": float(loss.detach())}
 
+    def train_graph(use_tdg):
+        """The same training with one step captured as a CUDA graph and replayed
+        (no host work per step: what the GPU takes for the step's kernels)."""
+        ws = [w.clone().requires_grad_() for w in init]
+
+        def step():
+            h = X
+            for k, w in enumerate(ws):
+                h = ag.tdg_matmul(h, w, **opts) if use_tdg else h @ w
+                if k < 2:
+                    h = torch.tanh(h)
+            loss = torch.nn.functional.cross_entropy(h, labels)
+            for w in ws:
+                w.grad = None
+            loss.backward()
+            with torch.no_grad():
+                for w in ws:
+                    w -= 0.1 * w.grad
+            return loss
+
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step()
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            loss = step()
+        graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return {"ms_per_step": e0.elapsed_time(e1) / steps, "loss": float(loss.detach()),
+                "steps_trained": steps + 4}
+
     ag.clear_plan_cache()
     out = {"torch fp32": train(False), "tdgemm 20 dB": train(True)}
+    for name, use in (("torch fp32, CUDA graph", False), ("tdgemm 20 dB, CUDA graph", True)):
+        try:
+            out[name] = train_graph(use)
+        except Exception as e:          # reported, not hidden
+            out[name] = {"error": str(e)[:300]}
     out["tdgemm 20 dB"]["products"] = {
         f"{k[0]}x{k[1]}x{k[2]} {k[3]}{k[4]}": p.info()["W_used"] for k, p in ag._plans.items()}
     ag.clear_plan_cache()

@@ -354,6 +354,82 @@ def compander(m: np.ndarray, gamma: int) -> tuple[np.ndarray, np.ndarray]:
 
 
 # --------------------------------------------------------------------------
+# pair-exact companders (eq. 26 per subblock product)
+# --------------------------------------------------------------------------
+def pair_companders(stA: BlockStats, stB: BlockStats, L: int, R: int):
+    """Eq. 26 for every subblock product (i, l, j) within the call's R_max:
+    rho_ilj = sqrt(T2 / T1) with T1 = sigma_A,il^2 m_B,lj^2 and
+    T2 = sigma_B,lj^2 m_A,il^2 (1 where either is zero), Gamma_A,ilj,
+    Gamma_B,ilj = split_gammas(R, L, rho_ilj), then c = Gamma / max|x| and
+    s = 1 / c per block of the pair (0 for an all-zero block).  Arrays indexed
+    [i, l, j]."""
+    nM, nK = stA.m.shape
+    nN = stB.m.shape[1]
+    cA = np.zeros((nM, nK, nN))
+    cB = np.zeros((nM, nK, nN))
+    sA = np.zeros((nM, nK, nN))
+    sB = np.zeros((nM, nK, nN))
+    for i in range(nM):
+        for l in range(nK):
+            for j in range(nN):
+                ma, mb = float(stA.m[i, l]), float(stB.m[l, j])
+                t1 = float(stA.var[i, l]) * (mb * mb)
+                t2 = float(stB.var[l, j]) * (ma * ma)
+                rho = math.sqrt(t2 / t1) if (t1 > 0.0 and t2 > 0.0) else 1.0
+                gA, gB = split_gammas(R, L, rho)
+                if ma > 0:
+                    cA[i, l, j] = float(gA) / ma
+                    sA[i, l, j] = 1.0 / cA[i, l, j]
+                if mb > 0:
+                    cB[i, l, j] = float(gB) / mb
+                    sB[i, l, j] = 1.0 / cB[i, l, j]
+    return cA, cB, sA, sB
+
+
+def tdgemm_pair_exact(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str,
+                      plan: Plan, alpha: float = 1.0, beta: float = 0.0,
+                      C_in: np.ndarray | None = None) -> np.ndarray:
+    """Symmetric companded-and-packed product with the companders of
+    ``pair_companders`` (the call's q and R_max from ``plan``): for every
+    output block (i, j), op(A)'s row block i is companded with c_A,ilj and
+    op(B)'s column block j with c_B,ilj for each slab l, then packed (eqs. 6-7),
+    multiplied, unpacked (eqs. 9-10) and summed over l with (s_A,ilj s_B,ilj)
+    exactly as ``tdgemm`` does for one block pair."""
+    T = NP_T[dtype]
+    A = np.ascontiguousarray(A, dtype=T)
+    B = np.ascontiguousarray(B, dtype=T)
+    M, K = A.shape
+    N = B.shape[1]
+    nM, nK, nN = -(-M // L), -(-K // L), -(-N // L)
+    stA, stB = block_stats(A, L), block_stats(B, L)
+    cA, cB, sA, sB = pair_companders(stA, stB, L, plan.R)
+    z = math.ldexp(1.0, -plan.q)
+    Q = math.ldexp(1.0, plan.q)
+    P = -(-L // W)
+    C = np.empty((M, N), dtype=T)
+    fn = getattr(lib(), f"orc_sym_gemm_{dtype}")
+    for i in range(nM):
+        r0, r1 = i * L, min(M, (i + 1) * L)
+        for j in range(nN):
+            c0, c1 = j * L, min(N, (j + 1) * L)
+            Ab = np.ascontiguousarray(A[r0:r1])
+            Bb = np.ascontiguousarray(B[:, c0:c1])
+            Aq = compand(Ab, L, cA[i, :, j].reshape(1, nK), dtype)
+            Bq = compand(Bb, L, cB[i, :, j].reshape(nK, 1), dtype)
+            Abar = pack_cols(Aq, L, W, z, dtype)                                           # eq. 6
+            Bbar = np.ascontiguousarray(pack_cols(np.ascontiguousarray(Bq.T), L, W, Q, dtype).T)  # eq. 7
+            sAb = np.ascontiguousarray(sA[i, :, j].reshape(1, nK))
+            sBb = np.ascontiguousarray(sB[i, :, j].reshape(nK, 1))
+            Cb = np.empty((r1 - r0, c1 - c0), dtype=T)
+            fn(_p(Abar), _p(Bbar), _i64(r1 - r0), _i64(c1 - c0), _i64(nK), _int(P), _int(L),
+               _int(plan.q), _p(sAb), _p(sBb), _i64(0), _i64(r1 - r0), _i64(0), _i64(c1 - c0),
+               ctypes.c_void_p(0), _p(Cb))
+            C[r0:r1, c0:c1] = Cb
+    Cin = None if C_in is None else C_in
+    return epilogue(C, alpha, beta, Cin, dtype)
+
+
+# --------------------------------------------------------------------------
 # Sec. 6: throughput/distortion control per inner kernel
 # --------------------------------------------------------------------------
 def kernel_ratios(stA: BlockStats, stB: BlockStats, L: int, gA: int, gB: int, s: float,

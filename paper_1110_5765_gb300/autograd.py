@@ -9,6 +9,7 @@ The quantizer is straight-through: its derivative is taken as the identity,
 so the backward products see the incoming gradient and the saved (unquantized)
 inputs; each backward product is companded and packed on its own, with
 companders and packing chosen from its own block statistics (Sec. 5, Sec. 6).
+The two adjoints of one product run on two streams.
 
 Plans (device workspace) are cached per shape, layout and options.
 """
@@ -31,6 +32,18 @@ def _op_layout(X: torch.Tensor):
         return "T", s1, X.t()
     X = X.contiguous()
     return "N", c, X
+
+
+_side: dict = {}
+
+
+def _side_stream(device) -> "torch.cuda.Stream":
+    key = torch.device(device).index
+    st = _side.get(key)
+    if st is None:
+        st = torch.cuda.Stream(device=device)
+        _side[key] = st
+    return st
 
 
 def _plan_for(M, N, K, tA, tB, lda, ldb, opts) -> Plan:
@@ -71,8 +84,24 @@ class TDGemmFn(torch.autograd.Function):
     def backward(ctx, dC):
         A, B = ctx.saved_tensors
         dC = dC.contiguous()
-        dA = product(dC, B.t(), ctx.opts) if ctx.needs_input_grad[0] else None
-        dB = product(A.t(), dC, ctx.opts) if ctx.needs_input_grad[1] else None
+        need_a, need_b = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_a and need_b):
+            dA = product(dC, B.t(), ctx.opts) if need_a else None
+            dB = product(A.t(), dC, ctx.opts) if need_b else None
+            return dA, dB, None
+        # the two adjoints are independent: dB on a side stream, so one
+        # product's latency-bound steps (statistics, fp64 planner, packing)
+        # overlap the other's
+        cur = torch.cuda.current_stream(dC.device)
+        side = _side_stream(dC.device)
+        side.wait_stream(cur)
+        dA = product(dC, B.t(), ctx.opts)
+        with torch.cuda.stream(side):
+            dB = product(A.t(), dC, ctx.opts)
+        cur.wait_stream(side)
+        A.record_stream(side)
+        dC.record_stream(side)
+        dB.record_stream(cur)
         return dA, dB, None
 
 

@@ -506,3 +506,62 @@ def test_kernel_snr_prediction_against_measurement(orc, gen):
             blk = (slice(i * L, (i + 1) * L), slice(j * L, (j + 1) * L))
             d = orc.snr_db(full.C[blk], ref[blk]) - pred[i, j]
             assert lo < d < hi, (i, j, d)
+
+
+# ------------------------------------------------------------------ pair-exact companders (eq. 26)
+def test_pair_exact_equals_separable_when_blocks_agree(orc):
+    """Every block of A alike (and every block of B alike): each pair's
+    rho_ilj is the global rho, so the pair-exact product equals the separable
+    product with the eq. 26 split of the same R_max, bit for bit."""
+    L = 32
+    a = synth.gaussian((L, L), 61, np.float64)
+    b = synth.laplace((L, L), 62, np.float64)
+    A = np.tile(a, (3, 4))
+    B = np.tile(b, (4, 2))
+    st = orc.load_s_table()
+    base = orc.tdgemm(A, B, L=L, W=2, dtype="f64", form="sym", bits=9, s_table=st)
+    stA, stB = orc.block_stats(A, L), orc.block_stats(B, L)
+    ag = orc.aggregates(stA, stB, L)
+    gA, gB = orc.split_gammas(base.plan.R, L, ag.rho)
+    sep = orc.tdgemm(A, B, L=L, W=2, dtype="f64", form="sym", gammas=(gA, gB))
+    assert sep.plan.q == base.plan.q
+    px = orc.tdgemm_pair_exact(A, B, L=L, W=2, dtype="f64", plan=base.plan)
+    assert np.array_equal(px.view(np.uint8), sep.C.view(np.uint8))
+
+
+def test_pair_exact_companders_follow_eq26(orc):
+    """Gamma_A,ilj / Gamma_B,ilj tracks rho_ilj = (sigma_B m_A)/(sigma_A m_B),
+    L Gamma_A Gamma_B never exceeds R_max, and a zero block gets c = s = 0."""
+    L = 32
+    A = synth.blockwise_crest((64, 96), 63, L, np.float64)
+    B = synth.blockwise_crest((96, 64), 64, L, np.float64)
+    A[:L, L:2 * L] = 0.0
+    stA, stB = orc.block_stats(A, L), orc.block_stats(B, L)
+    R = 32 * 200 * 180
+    cA, cB, sA, sB = orc.pair_companders(stA, stB, L, R)
+    assert np.all(cA[0, 1, :] == 0) and np.all(sA[0, 1, :] == 0)
+    for i in range(2):
+        for l in range(3):
+            for j in range(2):
+                if stA.m[i, l] == 0:
+                    continue
+                gA = round(cA[i, l, j] * stA.m[i, l])
+                gB = round(cB[i, l, j] * stB.m[l, j])
+                assert L * gA * gB <= R
+                rho = math.sqrt((stB.var[l, j] * stA.m[i, l] ** 2) / (stA.var[i, l] * stB.m[l, j] ** 2))
+                assert abs(gA * gA / (R / L) - rho) <= 2 * rho * (2.0 / gA)   # floor of sqrt
+                assert abs(sA[i, l, j] * cA[i, l, j] - 1.0) < 1e-15
+
+
+def test_pair_exact_beats_separable_on_unlike_blocks(orc):
+    """With blocks of different peak-to-RMS ratios the per-pair split lowers
+    the noise at the same R_max (the cross-term penalty the separable choice
+    pays), inside the headroom where only quantization noise remains."""
+    L = 64
+    A = synth.blockwise_crest((256, 512), 51, L, np.float64, kmax=11)
+    B = synth.blockwise_crest((512, 256), 52, L, np.float64, kmax=11)
+    ref = orc.exact_gemm(A, B)
+    sep = orc.tdgemm(A, B, L=L, W=2, dtype="f64", form="sym", bits=10)
+    px = orc.tdgemm_pair_exact(A, B, L=L, W=2, dtype="f64", plan=sep.plan)
+    assert sep.plan.W <= sep.plan.Wef
+    assert orc.snr_db(px, ref) > orc.snr_db(sep.C, ref) + 0.1
