@@ -406,6 +406,8 @@ def measure_forms(tdg, torch, A32, B32) -> dict:
         ("plain_f64", dict(dtype="f64", form="plain", W=1, bits=0), A64, B64),
         ("sym_f32_W2_20dB", dict(dtype="f32", form="sym", W=2, target_snr_db=20.0), A32, B32),
         ("asym_f32_W2_20dB", dict(dtype="f32", form="asym", W=2, target_snr_db=20.0), A32, B32),
+        ("sym_f32_W2_20dB_pair_exact", dict(dtype="f32", form="sym", W=2, target_snr_db=20.0,
+                                            pair_exact=True), A32, B32),
         ("sym_f32_W2_40dB", dict(dtype="f32", form="sym", W=2, target_snr_db=40.0), A32, B32),
         ("sym_f64_W2_40dB", dict(dtype="f64", form="sym", W=2, target_snr_db=40.0), A64, B64),
         ("sym_f64_W3_40dB", dict(dtype="f64", form="sym", W=3, target_snr_db=40.0), A64, B64),

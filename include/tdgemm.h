@@ -85,6 +85,12 @@ typedef enum {
                                     product (W = 1, Sec. 6) instead of failing  */
 #define TDG_KEEP_PACKED    0x2u  /* tdgemm_gemm also stores every packed slab
                                     result r_bar for tdgemm_unpack              */
+#define TDG_PAIR_EXACT     0x8u  /* companders of eq. 26 per subblock product (i, l, j)
+                                    within the call's R_max instead of one split
+                                    Gamma_A, Gamma_B per call; SYM form, transA =
+                                    transB = 'N', L = 128 (fp32) or 64 (fp64), W
+                                    in {2, 4} (target mode: W = 2); each CTA then
+                                    compands and packs its own operand tiles      */
 #define TDG_NOISE_RMS      0x4u  /* planner: scale the measured representation
                                     noise s(R_max, W) (taken with uniform integer
                                     inputs, Sec. 4.B) by 3 kappa_A kappa_B, the
@@ -122,7 +128,8 @@ typedef struct {
  *   target_snr_db   distortion target in dB (used when bits == 0)
  *   bits            > 0: fixed-bit companding, gamma = 2^(bits-1) - 1, W as
  *                   given (bits in 2..12; TC_INT up to 12)
- *   flags           TDG_ALLOW_FALLBACK | TDG_KEEP_PACKED | TDG_NOISE_RMS
+ *   flags           TDG_ALLOW_FALLBACK | TDG_KEEP_PACKED | TDG_NOISE_RMS |
+ *                   TDG_PAIR_EXACT
  *
  * On success *plan receives a new plan holding all device workspace for these
  * shapes (allocated on the current device).  On error *plan is left NULL.

@@ -18,6 +18,7 @@ DTYPES = {"f32": TDG_F32, "f64": TDG_F64}
 TDG_ALLOW_FALLBACK = 0x1
 TDG_KEEP_PACKED = 0x2
 TDG_NOISE_RMS = 0x4
+TDG_PAIR_EXACT = 0x8
 STATUS = {0: "TDG_OK", 1: "TDG_EINVAL", 2: "TDG_ENOMEM", 3: "TDG_ECUDA", 4: "TDG_EUNSUPPORTED",
           5: "TDG_EUNREACHABLE", 6: "TDG_ETIMEOUT", 7: "TDG_ENONFINITE", 8: "TDG_ESTATE"}
 

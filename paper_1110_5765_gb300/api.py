@@ -17,7 +17,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import DTYPES, FORMS, TDG_ALLOW_FALLBACK, TDG_KEEP_PACKED, TDG_NOISE_RMS, Info, check
+from ._lib import (DTYPES, FORMS, TDG_ALLOW_FALLBACK, TDG_KEEP_PACKED, TDG_NOISE_RMS,
+                   TDG_PAIR_EXACT, Info, check)
 
 _TORCH_DT = {"f32": torch.float32, "f64": torch.float64}
 _DT_OF = {torch.float32: "f32", torch.float64: "f64"}
@@ -90,7 +91,7 @@ class Plan:
                  transA: str = "N", transB: str = "N", lda: int | None = None,
                  ldb: int | None = None, ldc: int | None = None, allow_fallback: bool = True,
                  keep_packed: bool = False, rep_noise: str | dict | None = "package",
-                 noise_rms: bool = False):
+                 noise_rms: bool = False, pair_exact: bool = False):
         self._L = _lib.load()
         self.M, self.N, self.K = int(M), int(N), int(K)
         self.L, self.W, self.dtype, self.form = int(L), int(W), dtype, form
@@ -99,7 +100,7 @@ class Plan:
         self.ldb = ldb if ldb is not None else (self.N if transB == "N" else self.K)
         self.ldc = ldc if ldc is not None else self.N
         flags = ((TDG_ALLOW_FALLBACK if allow_fallback else 0) | (TDG_KEEP_PACKED if keep_packed else 0)
-                 | (TDG_NOISE_RMS if noise_rms else 0))
+                 | (TDG_NOISE_RMS if noise_rms else 0) | (TDG_PAIR_EXACT if pair_exact else 0))
         h = ctypes.c_void_p()
         check(self._L.tdgemm_plan(ctypes.byref(h), transA.encode(), transB.encode(), self.M,
                                   self.N, self.K, self.lda, self.ldb, self.ldc, self.L, self.W,

@@ -9,7 +9,7 @@ The quantizer is straight-through: its derivative is taken as the identity,
 so the backward products see the incoming gradient and the saved (unquantized)
 inputs; each backward product is companded and packed on its own, with
 companders and packing chosen from its own block statistics (Sec. 5, Sec. 6).
-The two adjoints of one product run on two streams.
+Inside CUDA-graph capture the two adjoints of one product run on two streams.
 
 Plans (device workspace) are cached per shape, layout and options.
 """
@@ -85,7 +85,10 @@ class TDGemmFn(torch.autograd.Function):
         A, B = ctx.saved_tensors
         dC = dC.contiguous()
         need_a, need_b = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        if not (need_a and need_b):
+        # two streams only inside CUDA-graph capture: replayed graphs carry no
+        # host cost, while in eager mode the extra stream bookkeeping costs
+        # more host time than the overlap saves on the device
+        if not (need_a and need_b) or not torch.cuda.is_current_stream_capturing():
             dA = product(dC, B.t(), ctx.opts) if need_a else None
             dB = product(A.t(), dC, ctx.opts) if need_b else None
             return dA, dB, None

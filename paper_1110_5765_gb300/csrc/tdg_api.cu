@@ -76,6 +76,7 @@ struct tdgemm_plan_s {
     double *mA, *eA, *mB, *eB, *sA, *sB, *stab, *agg;
     void *cA, *cB, *pair;
     void *Abuf, *Bbuf, *Rbar;
+    void *cApx = nullptr, *cBpx = nullptr, *pairpx = nullptr;   // TDG_PAIR_EXACT
     size_t Abuf_bytes, Bbuf_bytes;
     std::vector<double> stab_host;
     bool stab_dirty = false;
@@ -191,6 +192,19 @@ extern "C" tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB,
     tdg_status v = validate(transA, transB, M, N, K, lda, ldb, ldc, L, W, dtype, form,
                             target_snr_db, bits);
     if (v != TDG_OK) return v;
+    if (flags & TDG_PAIR_EXACT) {
+        const bool tn = (transA == 'N' || transA == 'n') && (transB == 'N' || transB == 'n');
+        if (form != TDG_SYM || !tn)
+            return fail(TDG_EINVAL, "TDG_PAIR_EXACT needs the SYM form with transA = transB = 'N'");
+        if (L != pair_exact_tile(dtype))
+            return fail(TDG_EINVAL, "TDG_PAIR_EXACT needs L = %d for this dtype",
+                        pair_exact_tile(dtype));
+        const bool fixed = bits > 0;
+        if (!(W == 2 || (fixed && W == 4)))
+            return fail(TDG_EINVAL, "TDG_PAIR_EXACT packs W = 2, or W = 4 with fixed bits");
+        if (flags & TDG_KEEP_PACKED)
+            return fail(TDG_EINVAL, "TDG_PAIR_EXACT does not keep packed slab results");
+    }
     tdgemm_plan_s *p = new tdgemm_plan_s();
     p->tA = (transA == 'T' || transA == 't') ? 'T' : 'N';
     p->tB = (transB == 'T' || transB == 't') ? 'T' : 'N';
@@ -221,6 +235,8 @@ extern "C" tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB,
     size_t o_cB = off; off += up(nBblk * p->esz);
     size_t o_pair = off; off += up((size_t)p->nK * p->nM * p->nN * p->esz);
     size_t o_stab = off; off += up((size_t)(kMaxW - 1) * kMaxLevels * 8);
+    const size_t npx = (flags & TDG_PAIR_EXACT) ? (size_t)p->nM * p->nK * p->nN : 0;
+    size_t o_px = off; off += up(3 * npx * p->esz);      // c_A, c_B, pair factors per (i, l, j)
     size_t abytes = 0, bbytes = 0, rbytes = 0;
     if (is_tc_form(form)) {
         const long long ldk = round_up(K, 128);
@@ -232,7 +248,7 @@ extern "C" tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB,
         // 21600): the packed slab products of a tile run on several CTAs and
         // the ordered sum over slabs in the unpack kernel; needs the r-bar
         // buffer that TDG_KEEP_PACKED also uses
-        if (is_packed_form(form) && !(flags & TDG_KEEP_PACKED) && p->nK >= 4) {
+        if (is_packed_form(form) && !(flags & (TDG_KEEP_PACKED | TDG_PAIR_EXACT)) && p->nK >= 4) {
             int bxa, bxb, bk, dev = 0, sms = 0;
             packed_gemm_boxes(dtype, form == TDG_SYM ? G_SYM : G_ASYM, &bxa, &bxb, &bk);
             cudaGetDevice(&dev);
@@ -279,6 +295,11 @@ extern "C" tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB,
     p->sA = (double *)(p->ws + o_sA); p->sB = (double *)(p->ws + o_sB);
     p->cA = p->ws + o_cA; p->cB = p->ws + o_cB; p->pair = p->ws + o_pair;
     p->stab = (double *)(p->ws + o_stab);
+    if (npx) {
+        p->cApx = p->ws + o_px;
+        p->cBpx = p->ws + o_px + npx * p->esz;
+        p->pairpx = p->ws + o_px + 2 * npx * p->esz;
+    }
     p->Abuf = p->ws + o_A; p->Bbuf = p->ws + o_B;
     p->Abuf_bytes = abytes; p->Bbuf_bytes = bbytes;
     p->Rbar = rbytes ? p->ws + o_R : nullptr;
@@ -320,8 +341,9 @@ extern "C" tdg_status tdgemm_set_kernel_control(tdgemm_plan_t p, int mode, doubl
     if (p->form != TDG_SYM) return fail(TDG_EINVAL, "inner-kernel control needs the SYM form");
     if (p->mode == MODE_MANUAL) return fail(TDG_EINVAL, "inner-kernel control needs a planned (not manual) plan");
     if (mode != 1 && mode != 2) return fail(TDG_EINVAL, "mode must be 0, 1 (SNR) or 2 (fraction)");
-    if (p->flags & TDG_KEEP_PACKED)
-        return fail(TDG_EINVAL, "inner-kernel control does not keep packed slab results");
+    if (p->flags & (TDG_KEEP_PACKED | TDG_PAIR_EXACT))
+        return fail(TDG_EINVAL,
+                    "inner-kernel control works without TDG_KEEP_PACKED and TDG_PAIR_EXACT");
     if (!isfinite(value)) return fail(TDG_EINVAL, "value must be finite");
     if (mode == 2 && (value < 0.0 || value > 1.0)) return fail(TDG_EINVAL, "fraction must be in [0, 1]");
     {
@@ -424,6 +446,10 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
     const double *stab = p->have_table ? p->stab : nullptr;
     CU_TRY(launch_planner<T>(pp, p->mA, p->eA, p->mB, p->eB, stab, p->dplan, p->agg, (T *)p->cA,
                              p->sA, (T *)p->cB, p->sB, (T *)p->pair, st));
+    const bool px = (p->flags & TDG_PAIR_EXACT) != 0;
+    if (px)
+        CU_TRY(launch_px_scales<T>(pp, p->mA, p->eA, p->mB, p->eB, p->dplan, (T *)p->cApx,
+                                   (T *)p->cBpx, (T *)p->pairpx, st));
     if (p->kctrl_mode) {
         CU_TRY(launch_kernel_control(pp, p->mA, p->eA, p->mB, p->eB, p->dplan, p->kctrl_mode,
                                      p->kctrl_thr, p->kctrl_k, p->kratio, p->kmask, st));
@@ -461,6 +487,8 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
                 if (!directB && !reuse_b)
                     CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, nullptr), 1, p->dplan, 1, 0,
                                             (T *)p->Bbuf, s.b_ld, s.b_rows, st));
+            } else if (px) {
+                // each CTA compands and packs its own tiles from A and B
             } else if (p->form == TDG_SYM) {
                 CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w, -1,
                                         (T *)p->Abuf, s.a_ld, s.a_rows, st));                   // eq. 6
@@ -561,7 +589,19 @@ static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cu
             plain_ops(p->kA, p->kB, ops.pa, ops.pb);
             g.kmask = p->kmask;
         }
-        cudaError_t e = launch_packed_gemm<T>(gform, Wk, g, ops, st);
+        cudaError_t e;
+        if (!plain && (p->flags & TDG_PAIR_EXACT)) {
+            GemmOperands raw{};
+            raw.a = {p->A_user, p->K, p->M, p->lda};      // op(A) row-major [M][K]
+            raw.b = {p->B_user, p->N, p->K, p->ldb};      // op(B) row-major [K][N]
+            g.pair = (const T *)p->pairpx;
+            g.cApx = (const T *)p->cApx;
+            g.cBpx = (const T *)p->cBpx;
+            g.P = p->L / Wk;
+            e = launch_px_gemm<T>(Wk, g, raw, st);
+        } else {
+            e = launch_packed_gemm<T>(gform, Wk, g, ops, st);
+        }
         if (e == cudaErrorInvalidValue)
             return fail(TDG_ECUDA, "packed GEMM: an operand could not be mapped for TMA");
         if (e != cudaSuccess)

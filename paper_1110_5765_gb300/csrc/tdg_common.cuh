@@ -87,6 +87,20 @@ __host__ __device__ inline int w_ef(long long R, int q, int p) {
     return 1 + fl;
 }
 
+// integer compander split of eq. 26 for a budget R: gA = floor(sqrt((R/L) rho))
+__device__ inline void split_gammas(long long R, int L, double rho, int &gA, int &gB) {
+    long long G = R / L;
+    if (G < 1) { gA = gB = 0; return; }
+    double v = __dsqrt_rn(__dmul_rn(__ddiv_rn((double)R, (double)L), rho));
+    long long a = (long long)floor(v);
+    if (a < 1) a = 1;
+    if (a > G) a = G;
+    long long b = R / ((long long)L * a);
+    if (b < 1) b = 1;
+    gA = (int)min(a, (long long)INT32_MAX);
+    gB = (int)min(b, (long long)INT32_MAX);
+}
+
 // ---------------------------------------------------------------------------
 // PTX helpers: shared-memory addresses, mbarriers, TMA
 // ---------------------------------------------------------------------------

@@ -86,6 +86,7 @@ struct GemmArgs {
     // CTA tile whose kernel's mask is 0 computes the conventional product from
     // the plain operands in the same launch.
     const unsigned char *kmask;
+    const T *cApx, *cBpx;   // pair-exact companders [(i nK + l) nN + j] (else unused)
     int ntn;                // set by the launcher: tiles per row of the 1-D tile grid
     long long ntiles;       // set by the launcher: tiles in the grid
     // slab splitting (needs Rbar): > 1 asks for that many groups of slabs, each
@@ -118,6 +119,20 @@ struct GemmOperands {
 template <typename T>
 cudaError_t launch_packed_gemm(int form, int W, const GemmArgs<T> &g, const GemmOperands &ops,
                                cudaStream_t st);
+
+// Pair-exact companders (eq. 26 per (i, l, j)): c_A, c_B per pair and the
+// de-companding factors, then the symmetric product with per-CTA companding
+// and packing (one L x L output block per CTA, L = pair_exact_tile(dtype),
+// W in {2, 4}, op(A) and op(B) row-major through ops.a = {A, K, M, lda} and
+// ops.b = {B, N, K, ldb}).
+int pair_exact_tile(int dtype);
+int pair_exact_bk();
+template <typename T>
+cudaError_t launch_px_scales(const PlanParams &pp, const double *mA, const double *vA,
+                             const double *mB, const double *vB, const DevPlan *plan, T *cA,
+                             T *cB, T *pair, cudaStream_t st);
+template <typename T>
+cudaError_t launch_px_gemm(int W, const GemmArgs<T> &g, const GemmOperands &ops, cudaStream_t st);
 
 // Tile shape the packed GEMM uses for (T, form): operand boxes are
 // {box_x_a, bk} for A and {box_x_b, bk} for B.
