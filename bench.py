@@ -747,6 +747,48 @@ def mlp_study(out_path=None, steps=50):
     return out
 
 
+def pair_exact_study(out_path=None):
+    """Pair-exact companders (eq. 26 per subblock product) against the
+    separable default at the same plan: effective GFLOP/s of the whole path
+    and SNR against fp64, on the benchmark input (uniform), on blocks of unlike
+    peak-to-RMS ratios (synth.blockwise_crest), fp32 at the 20 dB target and
+    fp64 with 10-bit companders inside the error-free region."""
+    import torch
+    from paper_1110_5765_gb300 import build as b
+    b.build()
+    import paper_1110_5765_gb300 as tdg
+    n = N_SIZE
+    flops = 2.0 * n ** 3
+    recs = []
+    cases = [("f32 uniform[-1,1], 20 dB", "f32", 128, dict(target_snr_db=20.0),
+              lambda s, T: synth.uniform((n, n), s, T)),
+             ("f32 block crest, 20 dB", "f32", 128, dict(target_snr_db=20.0),
+              lambda s, T: synth.blockwise_crest((n, n), s, 128, T)),
+             ("f64 block crest, 10 bits", "f64", 64, dict(bits=10),
+              lambda s, T: synth.blockwise_crest((n, n), s, 64, T))]
+    for name, dtype, L, kw, gen in cases:
+        T = np.float32 if dtype == "f32" else np.float64
+        A = torch.from_numpy(gen(3101, T)).cuda()
+        B = torch.from_numpy(gen(3102, T)).cuda()
+        ref = torch.matmul(A.double(), B.double())
+        C = torch.empty_like(A)
+        for px in (False, True):
+            p = tdg.Plan(n, n, n, L=L, W=2, dtype=dtype, form="sym", pair_exact=px, **kw)
+            t = _time(lambda: p.run(A, B, C), torch, reps=1 if dtype == "f64" else 3)
+            info = p.info()
+            p.close()
+            rec = {"case": name, "companders": "pair-exact" if px else "separable",
+                   "W_used": info["W_used"], "gflops": flops / t / 1e9, "ms": t * 1e3,
+                   "snr_db": tdg.snr_db(C, ref)}
+            recs.append(rec)
+            print(json.dumps(rec), flush=True)
+        del ref
+    if out_path:
+        with open(out_path, "w") as f:
+            json.dump(recs, f)
+    return recs
+
+
 def measure_precision_form(tdg, torch) -> dict:
     """The precision-form workload: 8192^3 Laplacian(b = 1) fp32, L = 128,
     tensor-core forms and the packed CUDA-core forms at a 40 dB target, beside
@@ -804,6 +846,8 @@ def main():
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--sweep", default=None, metavar="OUT.json",
                     help="run the 4096^3 distortion sweep (168 runs) and write its records")
+    ap.add_argument("--pairx", default=None, metavar="OUT.json",
+                    help="pair-exact against separable companders at 4096^3")
     ap.add_argument("--mlp", default=None, metavar="OUT.json",
                     help="time MLP training through the autograd form (config 4)")
     ap.add_argument("--pca2d", default=None, metavar="OUT.json",
@@ -819,6 +863,9 @@ def main():
         return
     if args.mlp:
         mlp_study(args.mlp)
+        return
+    if args.pairx:
+        pair_exact_study(args.pairx)
         return
     if args.sweep:
         sweep(args.sweep)
