@@ -176,6 +176,33 @@ __device__ inline void tma_prefetch_desc(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
 }
 
+// Programmatic dependent launch.  Every kernel of the library starts by
+// waiting for the kernel before it in the stream to finish (its writes then
+// visible) and by letting the next kernel be scheduled, so a launch and the
+// ramp-up of its CTAs overlap the predecessor's tail.  No global memory is
+// touched before the wait; launched without the attribute both are no-ops.
+__device__ inline void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// launch with the programmatic-stream-serialization attribute
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // record a device-side failure in the plan (first writer wins)
 __device__ inline void raise_status(DevPlan *plan, int code) {
     atomicCAS(&plan->status, 0, code);

@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
                        const __grid_constant__ CUtensorMap mapB,
                        const __grid_constant__ CUtensorMap mapPA,
                        const __grid_constant__ CUtensorMap mapPB, const GemmArgs<T> g) {
+    pdl_entry();
     using Cfg = GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>;
     constexpr int RG = Cfg::RG, CG = Cfg::CG, NCACC = Cfg::NCACC;
     constexpr bool TMEMC = Cfg::TMEMC;
@@ -602,8 +603,8 @@ cudaError_t launch_grid(const GemmArgs<T> &g0, const GemmOperands &ops, cudaStre
         g.groups = 1;
     }
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)nblocks, Cfg::NT, Cfg::SMEM, st>>>(ma, mb, mpa, mpb, g);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3((unsigned)nblocks), dim3(Cfg::NT), Cfg::SMEM, st, ma, mb, mpa, mpb,
+                      g);
 }
 
 // KEEP (store every packed slab result for tdgemm_unpack) and MIX (Sec. 6

@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(256) pack_k_xc_kernel(Src<T> S, int P, const D
                                                         int expectW, int wsign, T *out,
                                                         long long ldo, long long rows_out,
                                                         int vec_ok) {
+    pdl_entry();
     if (expectW > 0 && plan->W != expectW) return;
     constexpr int VEC = VecT<T>::n;
     const T w = W > 1 ? pack_weight<T>(plan, wsign) : T(1);
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(256) pack_k_kc_kernel(Src<T> S, int P, const D
                                                         int expectW, int wsign, T *out,
                                                         long long ldo, long long rows_out,
                                                         int vec_ok) {
+    pdl_entry();
     if (expectW > 0 && plan->W != expectW) return;
     constexpr int VEC = VecT<T>::n;
     constexpr int NK = TILE * W;            // k values per tile row
@@ -219,6 +221,7 @@ template <typename T, int W>
 __global__ void __launch_bounds__(256) pack_x_kernel(Src<T> S, int P, const DevPlan *plan,
                                                      int expectW, int wsign, T *out,
                                                      long long ldo) {
+    pdl_entry();
     if (expectW > 0 && plan->W != expectW) return;
     constexpr int NX = TILE * W;
     constexpr int PITCH = TILE + 1;
@@ -300,6 +303,7 @@ __device__ inline void encode8(const float *v, unsigned char *dst) {
 template <int FP8>
 __global__ void __launch_bounds__(256) codes_kc_kernel(Src<float> S, unsigned char *out,
                                                        long long ldo, int vec_ok) {
+    pdl_entry();
     constexpr int ES = FP8 ? 1 : 2;
     const long long nk8 = (S.K + 7) / 8;
     const long long items = S.X * nk8;
@@ -331,6 +335,7 @@ __global__ void __launch_bounds__(256) codes_kc_kernel(Src<float> S, unsigned ch
 template <int FP8>
 __global__ void __launch_bounds__(256) codes_xc_kernel(Src<float> S, unsigned char *out,
                                                        long long ldo, int vec_ok) {
+    pdl_entry();
     constexpr int ES = FP8 ? 1 : 2;
     constexpr int T64 = 64;
     constexpr int PITCH = T64 + 4;               // floats
@@ -416,16 +421,19 @@ cudaError_t launch_pack_k_w(const PackOperand<T> &o, const DevPlan *plan, int ex
     if (o.sx == 1) {
         const int vec_ok = aligned_in && aligned_out && (o.sk % VEC == 0);
         const long long items = rows_out * ((o.X + VEC - 1) / VEC);
-        pack_k_xc_kernel<T, W><<<resident_grid((const void *)pack_k_xc_kernel<T, W>,
-                                               (items + 255) / 256, 4), 256, 0, st>>>(
-            S, P, plan, expectW, wsign, out, ldo, rows_out, vec_ok);
+        return launch_pdl(pack_k_xc_kernel<T, W>,
+                          dim3(resident_grid((const void *)pack_k_xc_kernel<T, W>,
+                                             (items + 255) / 256, 4)),
+                          dim3(256), 0, st, S, P, plan, expectW, wsign, out, ldo, rows_out,
+                          vec_ok);
     } else {
         const int vec_ok = aligned_in && (o.sx % VEC == 0) && o.sk == 1;
         const long long tiles = ((o.X + TILE - 1) / TILE) * ((o.K + o.L - 1) / o.L) *
                                 ((P + TILE - 1) / TILE);
-        pack_k_kc_kernel<T, W><<<resident_grid((const void *)pack_k_kc_kernel<T, W>, tiles, 4), 256,
-                                 0, st>>>(S, P, plan, expectW, wsign, out, ldo,
-                                                              rows_out, vec_ok);
+        return launch_pdl(pack_k_kc_kernel<T, W>,
+                          dim3(resident_grid((const void *)pack_k_kc_kernel<T, W>, tiles, 4)),
+                          dim3(256), 0, st, S, P, plan, expectW, wsign, out, ldo, rows_out,
+                          vec_ok);
     }
     return cudaGetLastError();
 }
@@ -437,7 +445,8 @@ cudaError_t launch_pack_x_w(const PackOperand<T> &o, const DevPlan *plan, int ex
     const int P = (o.L + W - 1) / W;
     const long long tiles = ((o.X + o.L - 1) / o.L) * ((P + TILE - 1) / TILE) *
                             ((o.K + TILE - 1) / TILE);
-    pack_x_kernel<T, W><<<capped(tiles), 256, 0, st>>>(S, P, plan, expectW, wsign, out, ldo);
+    return launch_pdl(pack_x_kernel<T, W>, dim3(capped(tiles)), dim3(256), 0, st, S, P, plan,
+                      expectW, wsign, out, ldo);
     return cudaGetLastError();
 }
 
@@ -476,14 +485,14 @@ cudaError_t launch_codes(const PackOperand<float> &o, int fp8, void *out, long l
         const int vec_ok = aligned && (o.sx % 4 == 0);
         const long long items = o.X * ((o.K + 7) / 8);
         const int g = capped((items + 255) / 256);
-        if (fp8) codes_kc_kernel<1><<<g, 256, 0, st>>>(S, ob, ldo, vec_ok);
-        else codes_kc_kernel<0><<<g, 256, 0, st>>>(S, ob, ldo, vec_ok);
+        return fp8 ? launch_pdl(codes_kc_kernel<1>, dim3(g), dim3(256), 0, st, S, ob, ldo, vec_ok)
+                   : launch_pdl(codes_kc_kernel<0>, dim3(g), dim3(256), 0, st, S, ob, ldo, vec_ok);
     } else {
         const int vec_ok = aligned && o.sx == 1 && (o.sk % 4 == 0);
         const long long tiles = ((o.X + 63) / 64) * ((o.K + 63) / 64);
         const int g = capped(tiles);
-        if (fp8) codes_xc_kernel<1><<<g, 256, 0, st>>>(S, ob, ldo, vec_ok);
-        else codes_xc_kernel<0><<<g, 256, 0, st>>>(S, ob, ldo, vec_ok);
+        return fp8 ? launch_pdl(codes_xc_kernel<1>, dim3(g), dim3(256), 0, st, S, ob, ldo, vec_ok)
+                   : launch_pdl(codes_xc_kernel<0>, dim3(g), dim3(256), 0, st, S, ob, ldo, vec_ok);
     }
     return cudaGetLastError();
 }

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(32) slab_aggregates_kernel(PlanParams pp,
                                                              const double *__restrict__ mB,
                                                              const double *__restrict__ vB,
                                                              double *__restrict__ agg) {
+    pdl_entry();
     if (pp.mode == MODE_MANUAL) return;
     const int l = blockIdx.x, lane = threadIdx.x;
     double X = 0, MA = 0, Y = 0, MB = 0;
@@ -142,6 +143,7 @@ static_assert(sizeof(LevelRec) == kLevelRecDoubles * sizeof(double), "planner wo
 __global__ void __launch_bounds__(32) level_kernel(PlanParams pp, const double *__restrict__ agg,
                                                    const double *__restrict__ stab,
                                                    LevelRec *__restrict__ res) {
+    pdl_entry();
     const int L = pp.L;
     int t_lo = 0;
     while (r_level(t_lo) < L) ++t_lo;
@@ -179,6 +181,7 @@ __global__ void __launch_bounds__(32) level_kernel(PlanParams pp, const double *
 __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
     PlanParams pp, const double *__restrict__ agg, const double *__restrict__ stab,
     const LevelRec *__restrict__ res, DevPlan *plan) {
+    pdl_entry();
     __shared__ unsigned long long best_n[kPlanThreads];
     __shared__ int best_t[kPlanThreads];
     __shared__ double tot[4];
@@ -315,6 +318,7 @@ template <typename T>
 __global__ void scales_kernel(PlanParams pp, const double *__restrict__ mA,
                               const double *__restrict__ mB, const DevPlan *__restrict__ plan,
                               T *cA, double *sA, T *cB, double *sB) {
+    pdl_entry();
     const long long nAblk = (long long)pp.nM * pp.nK, nBblk = (long long)pp.nK * pp.nN;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const DevPlan a = *plan;
@@ -337,6 +341,7 @@ template <typename T>
 __global__ void pairs_kernel(PlanParams pp, const double *__restrict__ sA,
                              const double *__restrict__ sB, const DevPlan *__restrict__ plan,
                              T *pair) {
+    pdl_entry();
     if (!needs_companders(pp, *plan)) return;
     const long long n = (long long)pp.nK * pp.nM * pp.nN;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -378,6 +383,7 @@ __global__ void kernel_ratio_kernel(PlanParams pp, const double *__restrict__ mA
                                     const double *__restrict__ vA, const double *__restrict__ mB,
                                     const double *__restrict__ vB, const DevPlan *__restrict__ plan,
                                     double *ratio) {
+    pdl_entry();
     const long long T = (long long)pp.nM * pp.nN;
     const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -414,6 +420,7 @@ __global__ void __launch_bounds__(kMaskThreads)
     kernel_mask_kernel(long long T, int mode, double thr, long long k,
                        const DevPlan *__restrict__ plan, const double *__restrict__ ratio,
                        unsigned char *mask) {
+    pdl_entry();
     __shared__ unsigned long long chunk[kMaskChunk];
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool fell_back = plan->W < 2;      // uniform
@@ -446,13 +453,12 @@ cudaError_t launch_kernel_control(const PlanParams &pp, const double *mA, const 
                                   int mode, double thr, long long k, double *ratio,
                                   unsigned char *mask, cudaStream_t st) {
     const long long T = (long long)pp.nM * pp.nN;
-    kernel_ratio_kernel<<<(int)((T * 32 + 255) / 256), 256, 0, st>>>(pp, mA, vA, mB, vB, plan,
-                                                                      ratio);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(kernel_ratio_kernel, dim3((unsigned)((T * 32 + 255) / 256)),
+                               dim3(256), 0, st, pp, mA, vA, mB, vB, plan, ratio);
     if (e != cudaSuccess) return e;
-    kernel_mask_kernel<<<(int)((T + kMaskThreads - 1) / kMaskThreads), kMaskThreads, 0, st>>>(
-        T, mode, thr, k, plan, ratio, mask);
-    return cudaGetLastError();
+    return launch_pdl(kernel_mask_kernel,
+                      dim3((unsigned)((T + kMaskThreads - 1) / kMaskThreads)), dim3(kMaskThreads),
+                      0, st, T, mode, thr, k, plan, (const double *)ratio, mask);
 }
 
 template <typename T>
@@ -463,8 +469,8 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
     // agg: 4 nK per-slab aggregates, then one record per candidate (W, level)
     LevelRec *res = reinterpret_cast<LevelRec *>(agg + 4 * (long long)pp.nK);
     if (pp.mode != MODE_MANUAL) {
-        slab_aggregates_kernel<<<pp.nK, 32, 0, st>>>(pp, mA, eA, mB, eB, agg);
-        cudaError_t e0 = cudaGetLastError();
+        cudaError_t e0 =
+            launch_pdl(slab_aggregates_kernel, dim3(pp.nK), dim3(32), 0, st, pp, mA, eA, mB, eB, agg);
         if (e0 != cudaSuccess) return e0;
     }
     if (pp.mode == MODE_TARGET && (pp.form == TDG_SYM || pp.form == TDG_ASYM)) {
@@ -473,23 +479,23 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
         const int nlev = (pp.p == 24 ? 4 * 24 : 4 * 40) - t_lo + 1;
         const int ctas = (pp.Wreq - 1) * ((nlev + 31) / 32);
         if (ctas > 0) {
-            level_kernel<<<ctas, 32, 0, st>>>(pp, agg, stab, res);
-            cudaError_t e1 = cudaGetLastError();
+            cudaError_t e1 = launch_pdl(level_kernel, dim3(ctas), dim3(32), 0, st, pp,
+                                        (const double *)agg, stab, res);
             if (e1 != cudaSuccess) return e1;
         }
     }
-    planner_kernel<<<1, kPlanThreads, 0, st>>>(pp, agg, stab, res, plan);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(planner_kernel, dim3(1), dim3(kPlanThreads), 0, st, pp,
+                               (const double *)agg, stab, (const LevelRec *)res, plan);
     if (e != cudaSuccess) return e;
     long long nblk = (long long)pp.nM * pp.nK + (long long)pp.nK * pp.nN;
     int g = (int)min((nblk + 255) / 256, 4096LL);
-    scales_kernel<T><<<g, 256, 0, st>>>(pp, mA, mB, plan, cA, sA, cB, sB);
-    e = cudaGetLastError();
+    e = launch_pdl(scales_kernel<T>, dim3(g), dim3(256), 0, st, pp, mA, mB, (const DevPlan *)plan,
+                   cA, sA, cB, sB);
     if (e != cudaSuccess) return e;
     long long np = (long long)pp.nK * pp.nM * pp.nN;
     g = (int)min((np + 255) / 256, 8192LL);
-    pairs_kernel<T><<<g, 256, 0, st>>>(pp, sA, sB, plan, pair);
-    return cudaGetLastError();
+    return launch_pdl(pairs_kernel<T>, dim3(g), dim3(256), 0, st, pp, (const double *)sA,
+                      (const double *)sB, (const DevPlan *)plan, pair);
 }
 
 template cudaError_t launch_planner<float>(const PlanParams &, const double *, const double *,

@@ -35,6 +35,7 @@ __global__ void px_scales_kernel(PlanParams pp, const double *__restrict__ mA,
                                  const double *__restrict__ vA, const double *__restrict__ mB,
                                  const double *__restrict__ vB, const DevPlan *__restrict__ plan,
                                  T *cA, T *cB, T *pair) {
+    pdl_entry();
     const long long R = plan->R;
     if (plan->W < 2) return;                       // conventional product chosen
     const long long n = (long long)pp.nM * pp.nK * pp.nN;
@@ -89,6 +90,7 @@ template <typename T, int W, typename C>
 __global__ void __launch_bounds__(PxCfg<T, W, C>::NT, sizeof(T) == 4 ? 2 : 1)
     px_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                    const __grid_constant__ CUtensorMap mapB, const GemmArgs<T> g) {
+    pdl_entry();
     using Cfg = PxCfg<T, W, C>;
     constexpr int BM = Cfg::BM, BN = Cfg::BN, TM = Cfg::TM, TN = Cfg::TN, BK = Cfg::BK;
     constexpr int STAGES = Cfg::STAGES, NT = Cfg::NT, RG = Cfg::RG, CG = Cfg::CG, KR = Cfg::KR;
@@ -296,8 +298,7 @@ cudaError_t launch_px_w(const GemmArgs<T> &g0, const GemmOperands &ops, cudaStre
     g.ntn = (int)((g.N + C::BN - 1) / C::BN);
     const long long ntiles = ((g.M + C::BM - 1) / C::BM) * g.ntn;
     if (ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)ntiles, Cfg::NT, Cfg::SMEM, st>>>(ma, mb, g);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3((unsigned)ntiles), dim3(Cfg::NT), Cfg::SMEM, st, ma, mb, g);
 }
 
 }  // namespace
@@ -311,8 +312,8 @@ cudaError_t launch_px_scales(const PlanParams &pp, const double *mA, const doubl
                              T *cB, T *pair, cudaStream_t st) {
     const long long n = (long long)pp.nM * pp.nK * pp.nN;
     const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
-    px_scales_kernel<T><<<grid, 256, 0, st>>>(pp, mA, vA, mB, vB, plan, cA, cB, pair);
-    return cudaGetLastError();
+    return launch_pdl(px_scales_kernel<T>, dim3(grid), dim3(256), 0, st, pp, mA, vA, mB, vB, plan,
+                      cA, cB, pair);
 }
 
 template <typename T>

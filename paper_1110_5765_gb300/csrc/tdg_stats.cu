@@ -74,6 +74,7 @@ struct StatsOp {
 template <typename T>
 __global__ void __launch_bounds__(256) block_stats_kernel(StatsOp<T> A, StatsOp<T> B, int L,
                                                           DevPlan *plan) {
+    pdl_entry();
     constexpr int VEC = 16 / sizeof(T);
     const bool isA = (long long)blockIdx.x < A.nblk;
     const StatsOp<T> &o = isA ? A : B;
@@ -198,8 +199,7 @@ cudaError_t launch_block_stats(const T *A, long long rows_a, long long cols_a, l
     StatsOp<T> ob = stats_op(B, rows_b, cols_b, ldb, L, trans_b, nbc_b, mxB, varB);
     const long long nb = oa.nblk + ob.nblk;
     if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    block_stats_kernel<T><<<(unsigned)nb, 256, 0, st>>>(oa, ob, L, plan);
-    return cudaGetLastError();
+    return launch_pdl(block_stats_kernel<T>, dim3((unsigned)nb), dim3(256), 0, st, oa, ob, L, plan);
 }
 
 #define TDG_STATS_INST(T)                                                                     \

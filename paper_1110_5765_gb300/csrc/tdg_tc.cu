@@ -150,6 +150,7 @@ template <int FP8>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                    const __grid_constant__ CUtensorMap mapB, const TcArgs g) {
+    pdl_entry();
     constexpr int BK = FP8 ? 128 : 64;          // k elements per stage
     constexpr int KSTEP_BYTES = 32;             // one MMA: 16 fp16 or 32 e4m3 values
     constexpr int MMAS_PER_STAGE = ROW_BYTES / KSTEP_BYTES;
@@ -382,16 +383,18 @@ static cudaError_t launch_tc(const TcArgs &a, const CUtensorMap &mapA, const CUt
     auto kern = tc_gemm_kernel<FP8>;
     static int max_clusters = 0;
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.blockDim = dim3(NUM_THREADS);
     cfg.dynamicSmemBytes = SMEM_BYTES;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 1;                    // the occupancy query: cluster shape only
     if (!max_clusters) {
         cudaError_t e =
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
@@ -407,6 +410,7 @@ static cudaError_t launch_tc(const TcArgs &a, const CUtensorMap &mapA, const CUt
     }
     const long long pairs = ((a.N + BN - 1) / BN) * (((a.M + BM - 1) / BM + 1) / 2);
     cfg.gridDim = dim3((unsigned)(2 * std::min<long long>(pairs, max_clusters)));
+    cfg.numAttrs = 2;                    // the launch: cluster shape and programmatic serialisation
     return cudaLaunchKernelEx(&cfg, kern, mapA, mapB, a);
 }
 

@@ -25,6 +25,7 @@ __device__ inline T rint_d(T v) {
 
 template <typename T, int ASYM>
 __global__ void unpack_kernel(GemmArgs<T> g, int W, int64_t *rint_out) {
+    pdl_entry();
     if (g.plan->W != W) return;            // the planner chose another packing
     const long long total = g.M * g.N;
     const int q = g.plan->q;
@@ -132,9 +133,8 @@ cudaError_t launch_unpack(int form, int W, const GemmArgs<T> &g, int64_t *rint_o
                           cudaStream_t st) {
     const long long total = g.M * g.N;
     const int grid = (int)min((total + 255) / 256, 152LL * 32);
-    if (form == G_ASYM) unpack_kernel<T, 1><<<grid, 256, 0, st>>>(g, W, rint_out);
-    else unpack_kernel<T, 0><<<grid, 256, 0, st>>>(g, W, rint_out);
-    return cudaGetLastError();
+    if (form == G_ASYM) return launch_pdl(unpack_kernel<T, 1>, dim3(grid), dim3(256), 0, st, g, W, rint_out);
+    return launch_pdl(unpack_kernel<T, 0>, dim3(grid), dim3(256), 0, st, g, W, rint_out);
 }
 
 template cudaError_t launch_unpack<float>(int, int, const GemmArgs<float> &, int64_t *,
