@@ -143,6 +143,21 @@ __device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// The same test, letting the hardware suspend the thread for up to hint_ns
+// while the phase is incomplete (for warps whose waits are long and whose
+// spinning would take issue slots from the warps they wait for)
+__device__ inline bool mbar_try_wait_suspend(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait on an mbarrier phase: gives up after `budget_ns` nanoseconds
 // of the global timer and returns false.
 __device__ inline uint64_t global_ns() {
@@ -158,6 +173,19 @@ __device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
     uint64_t start = global_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - start > kWaitBudgetNs) return false;
+    }
+}
+
+// bounded wait whose retries (and, with first_too, its first test) may
+// suspend the thread for up to 1 ms each
+__device__ inline bool mbar_wait_bounded_suspend(uint64_t *bar, uint32_t parity,
+                                                 bool first_too = false) {
+    if (first_too ? mbar_try_wait_suspend(bar, parity, 1000000u) : mbar_try_wait(bar, parity))
+        return true;
+    uint64_t start = global_ns();
+    while (true) {
+        if (mbar_try_wait_suspend(bar, parity, 1000000u)) return true;
         if (global_ns() - start > kWaitBudgetNs) return false;
     }
 }

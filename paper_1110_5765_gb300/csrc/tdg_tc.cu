@@ -10,24 +10,29 @@
 //
 // C = sum_l (s_A,il s_B,lj) * (A~_l B~_l^T), slabs l of L k-values.
 //
-// CTA tile 128 x 256, one persistent CTA per SM (192 KB of shared memory) that
-// walks its share of the output tiles, the pipeline running on across tiles.
-// CTAs run in clusters of two on vertically adjacent tiles (same 256 columns
-// of B~): each CTA loads its own 128 rows of A~ and one half of the B~ tile,
-// multicast into both CTAs' shared memory, so a pair reads B~ once from L2.
-//   warp 0      allocates 512 TMEM columns; lane 0 streams 128-byte-wide k
-//               boxes of A~ (128 rows) and its half of B~ (128 rows, to both
-//               CTAs) with 2-D TMA (128-byte swizzle) into a 4-deep ring;
-//   warp 1      lane 0 issues tcgen05.mma (M = 128, N = 256) into one of two
-//               TMEM accumulators, a fresh accumulation per slab, and
-//               commits to mbarriers that free ring stages (in both CTAs of
-//               the pair: a stage is refilled once both have consumed it) and
+// Output tiles of 256 x 256 are computed by pairs of SMs with the two-CTA
+// form of tcgen05.mma (cta_group::2, M = 256, N = 256): the CTAs of a
+// cluster of two each hold 128 rows of A~ and 128 rows (output columns) of
+// B~ in shared memory, and the pair's MMA reads both halves of both
+// operands, so each shared-memory byte loaded feeds both SMs' tensor cores.
+// Per SM and k-step that is a third less shared-memory traffic (TMA writes
+// and MMA reads) than a one-CTA 128 x 256 tile.  Each CTA's TMEM holds its
+// own 128 rows x 256 columns of the accumulator.  Persistent clusters walk
+// their share of the tile pairs, the pipeline running on across tiles.
+//   warp 0      allocates 512 TMEM columns (both CTAs, collectively); lane 0
+//               streams 128-byte-wide k boxes of this CTA's A~ and B~ halves
+//               with 2-D TMA (128-byte swizzle) into a 6-deep ring, both
+//               CTAs' copies completing on the even CTA's mbarrier;
+//   warp 1      (even CTA) lane 0 issues the pair's tcgen05.mma into one of
+//               two TMEM accumulators, a fresh accumulation per slab, and
+//               commits to mbarriers in both CTAs that free ring stages and
 //               hand a full slab to the epilogue;
 //   warps 2..17 epilogue: each thread owns one output row and 64 columns;
 //               per slab it reads its TMEM lane (tcgen05.ld), applies
 //               C_acc = fma(r, s_A s_B, C_acc) in fp32 and releases the
-//               accumulator, so the next-but-one slab's MMAs can reuse it
-//               while this one is being promoted.
+//               accumulator to the even CTA's MMA issuer, so the
+//               next-but-one slab's MMAs can reuse it while this one is
+//               being promoted.
 // Every wait is bounded (2 s of global time); on expiry the CTA records
 // TDG_ETIMEOUT, drains what it issued (bounded) and frees its TMEM.
 #include <cuda_fp16.h>
@@ -41,11 +46,13 @@ namespace tdg {
 
 namespace {
 
-constexpr int BM = 128, BN = 256;
-constexpr int STAGES = 4;
+constexpr int BM = 128, BN = 256;                  // per CTA: rows of A~, columns of C
+constexpr int BNH = BN / 2;                          // rows of B~ per CTA
+constexpr int STAGES = 6;
 constexpr int ROW_BYTES = 128;                       // k-bytes per stage (one swizzle row)
 constexpr int STAGE_A = BM * ROW_BYTES;              // 16 KB
-constexpr int STAGE_B = BN * ROW_BYTES;              // 32 KB
+constexpr int STAGE_B = BNH * ROW_BYTES;             // 16 KB
+constexpr uint32_t PAIR_TX = 2 * (STAGE_A + STAGE_B);   // bytes one stage brings into the pair
 constexpr int EPI_COLS = 64;                         // output columns per epilogue thread
 constexpr int EPI_WARPS = 4 * (BN / EPI_COLS);       // 4 TMEM lane quadrants x column groups
 constexpr int NUM_THREADS = 32 * (2 + EPI_WARPS);
@@ -65,44 +72,60 @@ __device__ inline uint64_t desc_sw128(uint32_t saddr) {
 }
 
 // instruction descriptor: D fp32, A/B fp16 (or E4M3 under kind::f8f6f4,
-// whose format code is also 0), both K-major, N = 256, M = 128
+// whose format code is also 0), both K-major, N = 256, M = 256 (the pair)
 constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+                           ((uint32_t)((2 * BM) >> 4) << 24);
 
+// the pair's MMA, issued by the even CTA: A rows 0..127 and B~ rows 0..127
+// from its shared memory, rows 128..255 of both from the peer's (same offsets)
 template <int FP8>
-__device__ inline void mma(uint32_t dtmem, uint64_t ad, uint64_t bd, int accumulate) {
+__device__ inline void mma2(uint32_t dtmem, uint64_t ad, uint64_t bd, int accumulate) {
     if constexpr (FP8) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
             "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate));
     } else {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
             "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate));
     }
 }
 
-// the same commit, arriving on the mbarrier at this offset in every CTA of
-// the cluster named in mask
-__device__ inline void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+// arrive on the mbarrier at bar's offset in both CTAs of the pair once the
+// pair's MMAs issued so far have completed
+__device__ inline void mma_commit_pair(uint64_t *bar) {
     asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
         " [%0], %1;" ::"r"(smem_u32(bar)),
-        "h"(mask)
+        "h"((uint16_t)0x3)
         : "memory");
 }
 
-// 2-D TMA load written to this offset in every CTA of the cluster named in
-// mask, each completing bytes on its own mbarrier at bar's offset
-__device__ inline void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
-                                      int y, uint16_t mask) {
+// 2-D TMA load into this CTA's shared memory, completing bytes on an
+// mbarrier that may sit in the peer CTA (bar_cl: shared::cluster address)
+__device__ inline void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar_cl, int x,
+                                        int y) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(bar_cl), "r"(x), "r"(y)
         : "memory");
+}
+
+// shared::cluster address of the variable at p's offset in CTA `rank`
+__device__ inline uint32_t cluster_addr(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+// arrive on an mbarrier given by its shared::cluster address (this CTA's or
+// the peer's).  The TMEM reads this releases are ordered by the tcgen05
+// fences around the arrive and the MMA issuer's wait.
+__device__ inline void mbar_arrive_cluster(uint32_t bar_cl) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar_cl) : "memory");
 }
 
 __device__ inline uint32_t cluster_rank() {
@@ -117,13 +140,6 @@ __device__ inline void cluster_sync() {
                  "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-__device__ inline void mma_commit(uint64_t *bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
-        : "memory");
-}
-
 __device__ inline void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -131,19 +147,32 @@ __device__ inline void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 32 lanes x 32 bits, 16 consecutive columns per thread
+// 32 lanes x 32 bits, 16 consecutive columns per thread (one load, then
+// the wait for it)
 __device__ inline void tmem_ld16(uint32_t taddr, float *v) {
     uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Waits.  Measured on GB300: the epilogue warps' waits for a finished slab
+// suspend between tests (spinning takes issue slots from the producer and
+// MMA warps); with E4M3 operands (one ring stage per slab) every wait of the
+// kernel suspending from its first test was faster still, with fp16 operands
+// slower, so the others spin there.
+template <int FP8>
+__device__ inline bool tc_wait(uint64_t *bar, uint32_t parity) {
+    return FP8 ? mbar_wait_bounded_suspend(bar, parity, true) : mbar_wait_bounded(bar, parity);
+}
+template <int FP8>
+__device__ inline bool tc_wait_epilogue(uint64_t *bar, uint32_t parity) {
+    return mbar_wait_bounded_suspend(bar, parity, FP8 != 0);
 }
 
 template <int FP8>
@@ -170,9 +199,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // persistent clusters of two: pair k of cluster c is c + k * (clusters),
-    // row-major over pairs of vertically adjacent 128 x 256 output tiles; this
-    // CTA takes the upper (rank 0) or lower (rank 1) tile of each pair
+    // row-major over 256 x 256 output tile pairs; this CTA holds the upper
+    // (rank 0) or lower (rank 1) 128 rows of each and the left or right half
+    // of its B~ rows
     const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
     const int cid = (int)blockIdx.x >> 1, ncl = (int)gridDim.x >> 1;
     const int tiles_n = (int)((g.N + BN - 1) / BN), tiles_m = (int)((g.M + BM - 1) / BM);
     const int npairs = tiles_n * ((tiles_m + 1) / 2);
@@ -186,29 +217,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         m0 = (long long)(2 * (t / tiles_n) + (int)rank) * BM;   // may pass M: zero rows
         n0 = (long long)(t % tiles_n) * BN;
     };
-    constexpr uint16_t kPair = 0x3;
 
+    // full[] and acc_empty[] are used in the even CTA only (arrivals from both
+    // CTAs); empty[] and acc_full[] in both (commits multicast to the pair)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 2);         // both CTAs' MMAs release the stage
+            mbar_init(&full[s], 1);          // the even CTA's expect_tx arrival
+            mbar_init(&empty[s], 1);         // the pair's MMA commit
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], EPI_WARPS);
+            mbar_init(&acc_empty[b], 2 * EPI_WARPS);   // epilogue warps of both CTAs
         }
         *abort_flag = 0;
         fence_barrier_init();
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+        // one warp of each CTA allocates collectively: the same columns in both
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
                      "r"(TMEM_COLS)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    // both CTAs' barriers exist before either multicasts or commits into them
+    // both CTAs' barriers exist before either copies, commits or arrives into them
     cluster_sync();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
@@ -221,7 +254,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int it = 0;
             for (; it < total; ++it) {
                 const int stage = it % STAGES;
-                if (it >= STAGES && !mbar_wait_bounded(&empty[stage], ((it / STAGES) + 1) & 1)) {
+                if (it >= STAGES && !tc_wait<FP8>(&empty[stage], ((it / STAGES) + 1) & 1)) {
                     raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);
                     *abort_flag = 1;
                     break;
@@ -232,25 +265,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const int kx = l * g.L + ks * BK;
                 long long m0, n0;
                 tile_origin(kt, m0, n0);
-                // own A~ rows; this CTA's half of B~ into both CTAs (the other
-                // half arrives from the peer): STAGE_A + STAGE_B bytes per CTA
-                mbar_arrive_expect_tx(&full[stage], STAGE_A + STAGE_B);
-                tma_load_2d(sA + stage * STAGE_A, &mapA, &full[stage], kx, (int)m0);
-                tma_load_2d_mc(sB + stage * STAGE_B + rank * (STAGE_B / 2), &mapB, &full[stage],
-                               kx, (int)(n0 + rank * (BN / 2)), kPair);
+                // this CTA's 128 rows of A~ and of B~; both CTAs' copies
+                // complete on the even CTA's full barrier, which expects them all
+                const uint32_t bar = cluster_addr(&full[stage], 0);
+                if (leader) mbar_arrive_expect_tx(&full[stage], PAIR_TX);
+                tma_load_2d_pair(sA + stage * STAGE_A, &mapA, bar, kx, (int)m0);
+                tma_load_2d_pair(sB + stage * STAGE_B, &mapB, bar, kx, (int)(n0 + rank * BNH));
             }
-            // every copy issued must land before the CTA can exit
+            // every copy issued must land before the CTA can exit: the pair's
+            // MMA released each of the last stages only after reading them
             for (int k = max(0, it - STAGES); k < it; ++k)
-                mbar_wait_bounded(&full[k % STAGES], (k / STAGES) & 1);
+                tc_wait<FP8>(&empty[k % STAGES], (k / STAGES) & 1);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             int it = 0;
             bool ok = true;
             for (int gs = 0; gs < my_tiles * nslab && ok; ++gs) {   // global slab count
                 const int b = gs & 1;
-                if (gs >= 2 && !mbar_wait_bounded(&acc_empty[b], ((gs >> 1) + 1) & 1)) {
+                if (gs >= 2 && !tc_wait<FP8>(&acc_empty[b], ((gs >> 1) + 1) & 1)) {
                     ok = false;
                     break;
                 }
@@ -258,7 +292,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const uint32_t d = tmem + (uint32_t)(b * BN);
                 for (int ks = 0; ks < slab_stages; ++ks, ++it) {
                     const int stage = it % STAGES;
-                    if (!mbar_wait_bounded(&full[stage], (it / STAGES) & 1)) {
+                    if (!tc_wait<FP8>(&full[stage], (it / STAGES) & 1)) {
                         ok = false;
                         break;
                     }
@@ -268,22 +302,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                     for (int kk = 0; kk < MMAS_PER_STAGE; ++kk) {
                         const uint64_t adv = (uint64_t)((kk * KSTEP_BYTES) >> 4);
-                        mma<FP8>(d, ad + adv, bd + adv, (ks | kk) != 0);
+                        mma2<FP8>(d, ad + adv, bd + adv, (ks | kk) != 0);
                     }
-                    mma_commit_mc(&empty[stage], kPair);   // frees the stage in both CTAs
+                    mma_commit_pair(&empty[stage]);     // frees the stage in both CTAs
                 }
                 if (!ok) break;
-                mma_commit(&acc_full[b]);               // the slab is complete in TMEM
+                mma_commit_pair(&acc_full[b]);          // the slab is complete in both TMEMs
             }
             if (!ok) {
                 raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);
                 *abort_flag = 1;
             }
-            // the last use of every stage released by both CTAs: this thread's
-            // MMAs are done (TMEM can be freed) and the peer's commits into
-            // this CTA's barriers have landed (it may exit)
+            // the last use of every stage released: the pair's MMAs are done
+            // (TMEM can be freed in both CTAs)
             for (int k = max(0, it - STAGES); k < it; ++k)
-                mbar_wait_bounded(&empty[k % STAGES], (k / STAGES) & 1);
+                tc_wait<FP8>(&empty[k % STAGES], (k / STAGES) & 1);
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -291,6 +324,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int quad = warp & 3;                     // TMEM lanes 32*quad .. +31
         const int cgrp = ew >> 2;                      // columns [EPI_COLS*cgrp, +EPI_COLS)
         const long long lstride = (long long)g.nM * g.nN;
+        const uint32_t acc_empty_cl[2] = {cluster_addr(&acc_empty[0], 0),
+                                          cluster_addr(&acc_empty[1], 0)};
         bool ok = true;
         for (int kt = 0; kt < my_tiles && ok; ++kt) {
             long long m0, n0;
@@ -311,7 +346,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const int b = gs & 1;
                 const float pr = pr_next;
                 if (l + 1 < nslab) pr_next = __ldg(prow + (long long)(l + 1) * lstride);
-                if (!mbar_wait_bounded(&acc_full[b], (gs >> 1) & 1)) { ok = false; break; }
+                if (!tc_wait_epilogue<FP8>(&acc_full[b], (gs >> 1) & 1)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t base =
                     tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN + cgrp * EPI_COLS);
@@ -319,13 +354,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
                     float v[16];
                     tmem_ld16(base + ch * 16, v);
+                    if (ch == EPI_COLS / 16 - 1) {
+                        // the accumulator is read: hand it back before the last fmas
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive_cluster(acc_empty_cl[b]);
+                    }
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
                         cacc[ch * 16 + e] = __fmaf_rn(v[e], pr, cacc[ch * 16 + e]);
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty[b]);
             }
             if (!ok) break;
             if (row < g.M) {
@@ -369,7 +407,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     cluster_sync();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS)
                      : "memory");
     }
@@ -421,7 +459,7 @@ cudaError_t launch_tc_gemm(int fp8, const TcArgs &a, const CUtensorMap &mapA,
 
 void tc_gemm_boxes(int fp8, int *box_rows_a, int *box_rows_b, int *box_k) {
     *box_rows_a = BM;
-    *box_rows_b = BN / 2;      // each CTA of a pair loads half of the B~ tile
+    *box_rows_b = BNH;         // each CTA of a pair loads half of the B~ tile
     *box_k = fp8 ? 128 : 64;
 }
 
