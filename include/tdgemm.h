@@ -228,7 +228,10 @@ tdg_status tdgemm_run(tdgemm_plan_t plan, const void *A, const void *B, void *C,
 /*
  * The same with HOST buffers: A, B and C are host pointers (pinned memory
  * gives asynchronous copies); the plan copies A and B to device staging
- * buffers it owns, runs, copies C back and synchronises `stream`.
+ * buffers it owns, runs, copies C back and synchronises `stream`.  When C is
+ * pinned memory the device can address, beta == 0 and the form is PLAIN, SYM
+ * or ASYM (without slab splitting or TDG_PAIR_EXACT), the GEMM writes C in
+ * place over the CPU-GPU link instead of a staged copy back.
  */
 tdg_status tdgemm_run_host(tdgemm_plan_t plan, const void *A, const void *B, void *C,
                            double alpha, double beta, void *stream);

@@ -671,12 +671,26 @@ extern "C" tdg_status tdgemm_run_host(tdgemm_plan_t p, const void *A, const void
         CU_TRY(cudaMalloc(&p->hB, bbytes));
         CU_TRY(cudaMalloc(&p->hC, cbytes));
     }
+    // C written by the GEMM's epilogue straight into host memory the device
+    // can address (pinned), in place of a copy back: where the CUDA-core
+    // packed GEMM kernel writes C (whole row segments per warp) and does not
+    // read it (beta = 0)
+    void *c_direct = nullptr;
+    if (beta == 0.0 && (is_packed_form(p->form) || p->form == TDG_PLAIN) &&
+        p->split_groups <= 1 && !(p->flags & TDG_PAIR_EXACT)) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, C) == cudaSuccess) {
+            if (at.type == cudaMemoryTypeHost && at.devicePointer) c_direct = at.devicePointer;
+        } else {
+            (void)cudaGetLastError();
+        }
+    }
     CU_TRY(cudaMemcpyAsync(p->hA, A, abytes, cudaMemcpyHostToDevice, st));
     CU_TRY(cudaMemcpyAsync(p->hB, B, bbytes, cudaMemcpyHostToDevice, st));
     if (beta != 0.0) CU_TRY(cudaMemcpyAsync(p->hC, C, cbytes, cudaMemcpyHostToDevice, st));
-    tdg_status r = tdgemm_run(p, p->hA, p->hB, p->hC, alpha, beta, stream);
+    tdg_status r = tdgemm_run(p, p->hA, p->hB, c_direct ? c_direct : p->hC, alpha, beta, stream);
     if (r != TDG_OK) return r;
-    CU_TRY(cudaMemcpyAsync(C, p->hC, cbytes, cudaMemcpyDeviceToHost, st));
+    if (!c_direct) CU_TRY(cudaMemcpyAsync(C, p->hC, cbytes, cudaMemcpyDeviceToHost, st));
     CU_TRY(cudaStreamSynchronize(st));
     return TDG_OK;
 }

@@ -345,6 +345,28 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         T *p = g.C + row * g.ldc + col;
         *p = g.beta_zero ? mul_rn(g.alpha, v) : fma_rn(g.alpha, v, mul_rn(g.beta, *p));
     };
+    // four adjacent columns (col % 4 == 0) as one 16- or 32-byte store where
+    // C allows it (beta = 0, aligned rows, all four inside): a warp then writes
+    // whole 256-byte row segments, which also keeps C written to host memory
+    // over the CPU link in full lines
+    auto store_c4 = [&](long long row, long long col, const T *v) {
+        const bool c_vec = g.beta_zero && (g.ldc % 4 == 0) &&
+                           ((reinterpret_cast<uintptr_t>(g.C) & (4 * sizeof(T) - 1)) == 0);
+        if (c_vec && row >= 0 && row < g.M && col + 4 <= g.N) {
+            T *p = g.C + row * g.ldc + col;
+            if constexpr (sizeof(T) == 4) {
+                *reinterpret_cast<float4 *>(p) =
+                    make_float4(mul_rn(g.alpha, v[0]), mul_rn(g.alpha, v[1]), mul_rn(g.alpha, v[2]),
+                                mul_rn(g.alpha, v[3]));
+            } else {
+                reinterpret_cast<double2 *>(p)[0] = make_double2(mul_rn(g.alpha, v[0]), mul_rn(g.alpha, v[1]));
+                reinterpret_cast<double2 *>(p)[1] = make_double2(mul_rn(g.alpha, v[2]), mul_rn(g.alpha, v[3]));
+            }
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) store_c(row, col + q, v[q]);
+    };
 
     int it = 0;
     bool ok = true;
@@ -524,7 +546,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         for (int i = 0; i < TM; ++i) {
             const long long row = out_row(i, 0);
 #pragma unroll
-            for (int j = 0; j < TN; ++j) store_c(row, out_col(j), acc[i][j]);
+            for (int j = 0; j < TN; j += 4) store_c4(row, out_col(j), &acc[i][j]);
         }
     } else if constexpr (TMEMC) {
         // ------------------------------------------------------------ store C
@@ -534,10 +556,21 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         for (int f0 = 0; f0 < Cfg::NC; f0 += 16) {
             float v[16];
             tmem_ld16(tcol + (uint32_t)f0, v);
+            if constexpr (NCACC == 1 && TN % 4 == 0) {
+                // 16 consecutive sums = four groups of four adjacent columns
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int eq = (f0 + q) / NCACC, dq = (f0 + q) % NCACC;
-                store_c(out_row(eq / TN, dq), out_col(eq % TN), (T)v[q]);
+                for (int q = 0; q < 16; q += 4) {
+                    T w[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) w[r] = (T)v[q + r];
+                    store_c4(out_row((f0 + q) / TN, 0), out_col((f0 + q) % TN), w);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int eq = (f0 + q) / NCACC, dq = (f0 + q) % NCACC;
+                    store_c(out_row(eq / TN, dq), out_col(eq % TN), (T)v[q]);
+                }
             }
         }
     } else {
@@ -548,8 +581,8 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
             for (int d = 0; d < NCACC; ++d) {
                 const long long row = out_row(i, d);
 #pragma unroll
-                for (int j = 0; j < TN; ++j)
-                    store_c(row, out_col(j), FORM == G_PLAIN ? acc[i][j] : cacc[d][i][j]);
+                for (int j = 0; j < TN; j += 4)
+                    store_c4(row, out_col(j), FORM == G_PLAIN ? &acc[i][j] : &cacc[d][i][j]);
             }
     }
     if constexpr (TMEMC) {
