@@ -789,6 +789,93 @@ def pair_exact_study(out_path=None):
     return recs
 
 
+def reuse_study(out_path=None):
+    """A product repeated with a fixed right operand (inference with fixed
+    weights): tdgemm_quantize_pack_a reuses B's statistics, companders and
+    packed form, so each call companders and packs only A.  Whole-path time of
+    a full pack + GEMM against an A-only pack + GEMM (L2 flushed before each
+    call, median of 20), with the reused result checked bit for bit against
+    the full one; at 4096^3 (uniform inputs) and for the forward pass of the
+    config-4 MLP (batch 4096, 128 -> 1024 -> 1024 -> 10, ReLU) with fixed
+    weights."""
+    import torch
+    from paper_1110_5765_gb300 import build as b
+    b.build()
+    import paper_1110_5765_gb300 as tdg
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def tmed(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    recs = []
+    forms = [("sym f32 W=2, 6-bit companders", dict(form="sym", W=2, bits=6)),
+             ("plain f32", dict(form="plain", W=1)),
+             ("tcgen05 integer, 8 bits", dict(form="tc_int", W=1, bits=8)),
+             ("tcgen05 E4M3", dict(form="tc_fp8", W=1))]
+    n = N_SIZE
+    A = torch.from_numpy(synth.uniform((n, n), 4101, np.float32)).cuda()
+    B = torch.from_numpy(synth.uniform((n, n), 4102, np.float32)).cuda()
+    C1, C2 = torch.empty_like(A), torch.empty_like(A)
+    for name, kw in forms:
+        p = tdg.Plan(n, n, n, L=L_BLOCK, dtype="f32", **kw)
+        full = tmed(lambda: (p.quantize_pack(A, B), p.gemm(C1)))
+        p.quantize_pack(A, B)
+        reuse = tmed(lambda: (p.quantize_pack(A), p.gemm(C2)))
+        torch.cuda.synchronize()
+        rec = {"case": f"{n}^3, {name}", "full_ms": full, "reuse_ms": reuse,
+               "saving": 1.0 - reuse / full, "same_bits": bool(torch.equal(C1, C2))}
+        recs.append(rec)
+        print(json.dumps(rec), flush=True)
+        p.close()
+    del A, B, C1, C2
+    batch, dims = 4096, (128, 1024, 1024, 10)
+    X = torch.from_numpy(synth.gaussian((batch, dims[0]), 4103, np.float32)).cuda()
+    Ws = [torch.from_numpy(synth.gaussian((dims[i], dims[i + 1]), 4104 + i, np.float32)).cuda()
+          * (2.0 / dims[i]) ** 0.5 for i in range(3)]
+    for name, kw in forms[0:1] + forms[3:4]:
+        plans = [tdg.Plan(batch, dims[i + 1], dims[i], L=L_BLOCK, dtype="f32", **kw)
+                 for i in range(3)]
+        outs = [torch.empty((batch, dims[i + 1]), device="cuda") for i in range(3)]
+
+        def fwd(reuse):
+            h = X
+            for i in range(3):
+                if reuse:
+                    plans[i].quantize_pack(h)
+                else:
+                    plans[i].quantize_pack(h, Ws[i])
+                plans[i].gemm(outs[i])
+                h = torch.relu(outs[i]) if i < 2 else outs[i]
+            return h
+        full = tmed(lambda: fwd(False))
+        y1 = fwd(False).clone()
+        reuse = tmed(lambda: fwd(True))
+        y2 = fwd(True)
+        torch.cuda.synchronize()
+        rec = {"case": f"MLP forward, batch {batch}, {dims}, {name}", "full_ms": full,
+               "reuse_ms": reuse, "saving": 1.0 - reuse / full,
+               "same_bits": bool(torch.equal(y1, y2))}
+        recs.append(rec)
+        print(json.dumps(rec), flush=True)
+        for p in plans:
+            p.close()
+    if out_path:
+        with open(out_path, "w") as f:
+            json.dump(recs, f)
+    return recs
+
+
 def measure_precision_form(tdg, torch) -> dict:
     """The precision-form workload: 8192^3 Laplacian(b = 1) fp32, L = 128,
     tensor-core forms and the packed CUDA-core forms at a 40 dB target, beside
@@ -852,9 +939,14 @@ def main():
                     help="time MLP training through the autograd form (config 4)")
     ap.add_argument("--pca2d", default=None, metavar="OUT.json",
                     help="run the 2DPCA face-recognition study (Sec. 8.A, Table 1)")
+    ap.add_argument("--reuse", default=None, metavar="OUT.json",
+                    help="run the fixed-right-operand (packed B reuse) study")
     ap.add_argument("--fig7", default=None, metavar="OUT.json",
                     help="run the 4096^3 inner-kernel throughput-control sweep (Sec. 6)")
     args = ap.parse_args()
+    if args.reuse:
+        reuse_study(args.reuse)
+        return
     if args.fig7:
         kernel_control_sweep(args.fig7)
         return
