@@ -418,6 +418,7 @@ def measure_forms(tdg, torch, A32, B32) -> dict:
         ("tc_fp8", dict(dtype="f32", form="tc_fp8", W=1, bits=0), A32, B32),
     ]
     out.update(measure_precision_form(tdg, torch))
+    out.update(measure_eigenface(tdg, torch))
     for name, kw, A, B in cases:
         try:
             p = tdg.Plan(n, n, n, L=L_BLOCK, **kw)
@@ -874,6 +875,39 @@ def reuse_study(out_path=None):
         with open(out_path, "w") as f:
             json.dump(recs, f)
     return recs
+
+
+def measure_eigenface(tdg, torch) -> dict:
+    """The eigenface-shaped workload: X = 10304 pixels x 4096 images, uniform
+    integers 0..255 with the pixel mean removed; the covariance C = X^T X
+    (4096 x 4096 x 10304, op(A) through the transpose flag) and the
+    projection of the 4096 images onto 400 orthonormal columns (4096 x 400 x
+    10304), sym fp32 W = 2 at 30 and 50 dB, beside cuBLAS fp32 (TF32 off).
+    SNR against the fp64 product."""
+    X = torch.from_numpy(synth.eigenface_pixels(10304, 4096, 7)).cuda()
+    U = torch.from_numpy(np.linalg.qr(synth.rng(8).standard_normal((10304, 400)))[0]
+                         .astype(np.float32)).cuda()
+    X64 = X.double()
+    out = {}
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for what, Bop, n_out in (("cov", X, 4096), ("proj", U, 400)):
+        flops = 2.0 * 4096 * n_out * 10304
+        ref = torch.matmul(X64.t(), Bop.double())
+        C = torch.empty((4096, n_out), device="cuda")
+        t = _time(lambda: torch.matmul(X.t(), Bop, out=C), torch)
+        out[f"eig_{what}_cublas_f32"] = {"gflops": flops / t / 1e9, "ms": t * 1e3,
+                                         "snr_db": tdg.snr_db(C, ref)}
+        for target in (30.0, 50.0):
+            p = tdg.Plan(4096, n_out, 10304, L=L_BLOCK, W=2, dtype="f32", form="sym",
+                         target_snr_db=target, transA="T", lda=4096)
+            t = _time(lambda: p.run(X, Bop, C), torch)
+            info = p.info()
+            p.close()
+            out[f"eig_{what}_sym_f32_W2_{int(target)}dB"] = {
+                "gflops": flops / t / 1e9, "ms": t * 1e3, "snr_db": tdg.snr_db(C, ref),
+                "W_used": info["W_used"], "pred_snr_db": info["pred_snr_db"]}
+        del ref
+    return out
 
 
 def measure_precision_form(tdg, torch) -> dict:
