@@ -26,6 +26,7 @@ import argparse
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -306,7 +307,7 @@ def run_gpu(args):
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
     achieved = gemm_flops / gemm_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
+                "frac": achieved / fp32_peak, "traffic": gemm_traffic(W_used),
                 "kernel": f"packed_gemm_kernel<float, {'SYM' if W_used > 1 else 'PLAIN'}, W={W_used}> (FP32 FMA pipe)",
                 "peak_source": (f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz "
                                 "(unit counts and maximum SM clock)"),
@@ -367,6 +368,38 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# sources that define the packed GEMM kernel: the DRAM traffic recorded from an
+# ncu capture is reported only while they are unchanged since the capture
+GEMM_SOURCES = ("tdg_gemm.cuh", "tdg_gemm_tiles.h", "tdg_gemm_f32.cu", "tdg_common.cuh",
+                "tdg_internal.h")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "packed_gemm_f32_sym_w2_4096_traffic.md")
+
+
+def gemm_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1110_5765_gb300", "csrc")
+    for name in GEMM_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def gemm_traffic(W_used):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of the timed
+    packed GEMM (4096^3 sym W = 2) from the committed ncu summary, or None when
+    the kernel sources changed since that capture (or W differs)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            text = f.read()
+    except OSError:
+        return None
+    vals = dict(re.findall(r"^(traffic_bytes_per_launch|sources_sha256|W): *(\S+)", text, re.M))
+    if W_used != int(vals.get("W", 0)) or vals.get("sources_sha256") != gemm_sources_sha256():
+        return None
+    return float(vals["traffic_bytes_per_launch"])
 
 
 def _time(fn, torch, reps=3):
