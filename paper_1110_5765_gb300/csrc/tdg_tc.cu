@@ -21,7 +21,7 @@
 // their share of the tile pairs, the pipeline running on across tiles.
 //   warp 0      allocates 512 TMEM columns (both CTAs, collectively); lane 0
 //               streams 128-byte-wide k boxes of this CTA's A~ and B~ halves
-//               with 2-D TMA (128-byte swizzle) into a 6-deep ring, both
+//               with 2-D TMA (128-byte swizzle) into a 5-deep ring, both
 //               CTAs' copies completing on the even CTA's mbarrier;
 //   warp 1      (even CTA) lane 0 issues the pair's tcgen05.mma into one of
 //               two TMEM accumulators, a fresh accumulation per slab, and
@@ -48,7 +48,7 @@ namespace {
 
 constexpr int BM = 128, BN = 256;                  // per CTA: rows of A~, columns of C
 constexpr int BNH = BN / 2;                          // rows of B~ per CTA
-constexpr int STAGES = 6;
+constexpr int STAGES = 5;                            // 4, 6 and 7 measured slower at 8192^3
 constexpr int ROW_BYTES = 128;                       // k-bytes per stage (one swizzle row)
 constexpr int STAGE_A = BM * ROW_BYTES;              // 16 KB
 constexpr int STAGE_B = BNH * ROW_BYTES;             // 16 KB
