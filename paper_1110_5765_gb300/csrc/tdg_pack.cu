@@ -332,44 +332,58 @@ __global__ void __launch_bounds__(256) codes_kc_kernel(Src<float> S, unsigned ch
 }
 
 // x contiguous in the input: 64 x 64 tiles transposed through shared memory
+// (s[k][x], pitch 65: the row-wise writes and the column-wise reads of the
+// store phase are free of bank conflicts).  A thread issues its four 16-byte
+// loads of a tile before it uses any of them.  256 threads per CTA.
 template <int FP8>
 __global__ void __launch_bounds__(256) codes_xc_kernel(Src<float> S, unsigned char *out,
                                                        long long ldo, int vec_ok) {
     pdl_entry();
     constexpr int ES = FP8 ? 1 : 2;
     constexpr int T64 = 64;
-    constexpr int PITCH = T64 + 4;               // floats
-    __shared__ float s[T64 * PITCH];             // s[x][k]
+    constexpr int PITCH = T64 + 1;               // floats
+    constexpr int NLD = T64 * (T64 / 4) / 256;   // float4 loads per thread and tile
+    constexpr int NST = T64 * (T64 / 8) / 256;   // 8-value stores per thread and tile
+    __shared__ float s[T64 * PITCH];             // s[k][x]
     const long long xt = (S.X + T64 - 1) / T64, kt = (S.K + T64 - 1) / T64;
     for (long long t = blockIdx.x; t < xt * kt; t += gridDim.x) {
         const long long x0 = (t % xt) * T64, k0 = (t / xt) * T64;
         const float c = S.c[(x0 / S.L) * S.cx + (k0 / S.L) * S.cl];
-        __syncthreads();
-        // load: 64 k-rows x 64 x-values, float4 along x
-        for (int e = threadIdx.x; e < T64 * (T64 / 4); e += blockDim.x) {
+        float v[NLD][4];
+#pragma unroll
+        for (int u = 0; u < NLD; ++u) {
+            const int e = threadIdx.x + u * 256;
             const int kr = e / (T64 / 4), xc = (e % (T64 / 4)) * 4;
             const long long k = k0 + kr, x = x0 + xc;
-            float v[4];
             if (k < S.K && vec_ok && x + 4 <= S.X) {
-                float4 a = __ldg(reinterpret_cast<const float4 *>(S.p + k * S.sk + x));
-                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(S.p + k * S.sk + x));
+                v[u][0] = a.x; v[u][1] = a.y; v[u][2] = a.z; v[u][3] = a.w;
             } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] = (k < S.K && x + i < S.X) ? S.p[k * S.sk + x + i] : 0.f;
+                for (int i = 0; i < 4; ++i)
+                    v[u][i] = (k < S.K && x + i < S.X) ? S.p[k * S.sk + x + i] : 0.f;
             }
+        }
+        __syncthreads();   // the previous tile's readers are done with s
 #pragma unroll
-            for (int i = 0; i < 4; ++i) s[(xc + i) * PITCH + kr] = __fmul_rn(v[i], c);
+        for (int u = 0; u < NLD; ++u) {
+            const int e = threadIdx.x + u * 256;
+            const int kr = e / (T64 / 4), xc = (e % (T64 / 4)) * 4;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s[kr * PITCH + xc + i] = __fmul_rn(v[u][i], c);
         }
         __syncthreads();
-        // store: rows x, 8 k per thread
-        for (int e = threadIdx.x; e < T64 * (T64 / 8); e += blockDim.x) {
+        // store: rows x, 8 k per item
+#pragma unroll
+        for (int u = 0; u < NST; ++u) {
+            const int e = threadIdx.x + u * 256;
             const int xr = e / (T64 / 8), kc = (e % (T64 / 8)) * 8;
             const long long x = x0 + xr, k = k0 + kc;
             if (x >= S.X || k >= ldo) continue;
-            float v[8];
+            float w[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = (k + i < S.K) ? s[xr * PITCH + kc + i] : 0.f;
-            encode8<FP8>(v, out + (x * ldo + k) * ES);
+            for (int i = 0; i < 8; ++i) w[i] = (k + i < S.K) ? s[(kc + i) * PITCH + xr] : 0.f;
+            encode8<FP8>(w, out + (x * ldo + k) * ES);
         }
     }
 }
