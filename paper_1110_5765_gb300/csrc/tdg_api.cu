@@ -250,7 +250,7 @@ extern "C" tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB,
         // buffer that TDG_KEEP_PACKED also uses
         if (is_packed_form(form) && !(flags & (TDG_KEEP_PACKED | TDG_PAIR_EXACT)) && p->nK >= 4) {
             int bxa, bxb, bk, dev = 0, sms = 0;
-            packed_gemm_boxes(dtype, form == TDG_SYM ? G_SYM : G_ASYM, &bxa, &bxb, &bk);
+            packed_gemm_boxes(dtype, form == TDG_SYM ? G_SYM : G_ASYM, W, &bxa, &bxb, &bk);
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             const long long mrows = form == TDG_ASYM ? (long long)p->nM * Pof(L, W) : M;
@@ -349,8 +349,8 @@ extern "C" tdg_status tdgemm_set_kernel_control(tdgemm_plan_t p, int mode, doubl
     {
         // the mixed launch runs both kinds of tile with one box shape
         int sa, sb, sk, pa, pb, pk;
-        packed_gemm_boxes(p->dtype, G_SYM, &sa, &sb, &sk);
-        packed_gemm_boxes(p->dtype, G_PLAIN, &pa, &pb, &pk);
+        packed_gemm_boxes(p->dtype, G_SYM, 2, &sa, &sb, &sk);
+        packed_gemm_boxes(p->dtype, G_PLAIN, 1, &pa, &pb, &pk);
         if (sa != pa || sb != pb || sk != pk)
             return fail(TDG_EUNSUPPORTED, "packed and plain tiles differ for this dtype");
         if (p->L % sa || p->L % sb)

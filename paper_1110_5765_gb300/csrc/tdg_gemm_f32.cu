@@ -14,6 +14,7 @@ cudaError_t launch_packed_gemm<float>(int form, int W, const GemmArgs<float> &g,
                                       const GemmOperands &ops, cudaStream_t st) {
     using S = TilesF32;
     using A = TilesF32Asym;
+    using A2 = TilesF32AsymW2;
     if (form == G_PLAIN) return go<G_PLAIN, 1, S>(g, ops, st);
     if (form == G_SYM) {
         switch (W) {
@@ -25,8 +26,8 @@ cudaError_t launch_packed_gemm<float>(int form, int W, const GemmArgs<float> &g,
     }
     if (form == G_ASYM) {
         switch (W) {
-            case 1: return go<G_ASYM, 1, A>(g, ops, st);
-            case 2: return go<G_ASYM, 2, A>(g, ops, st);
+            case 1: return go<G_ASYM, 1, A2>(g, ops, st);
+            case 2: return go<G_ASYM, 2, A2>(g, ops, st);
             case 3: return go<G_ASYM, 3, A>(g, ops, st);
             case 4: return go<G_ASYM, 4, A>(g, ops, st);
         }

@@ -36,9 +36,11 @@ cudaError_t launch_packed_gemm<double>(int form, int W, const GemmArgs<double> &
 
 // TMA boxes {BM, BK} for A and {BN, BK} for B, from the same tile table the
 // launches use
-void packed_gemm_boxes(int dtype, int form, int *box_x_a, int *box_x_b, int *bk) {
+void packed_gemm_boxes(int dtype, int form, int W, int *box_x_a, int *box_x_b, int *bk) {
     if (dtype == TDG_F64) {
         *box_x_a = TilesF64::BM; *box_x_b = TilesF64::BN; *bk = TilesF64::BK;
+    } else if (form == G_ASYM && W <= 2) {
+        *box_x_a = TilesF32AsymW2::BM; *box_x_b = TilesF32AsymW2::BN; *bk = TilesF32AsymW2::BK;
     } else if (form == G_ASYM) {
         *box_x_a = TilesF32Asym::BM; *box_x_b = TilesF32Asym::BN; *bk = TilesF32Asym::BK;
     } else {

@@ -15,7 +15,8 @@ struct Tiles {
 // packed f32x2 main loop; 96 KB of ring keeps two CTAs per SM)
 using TilesF32 = Tiles<128, 128, 8, 8, 32, 3>;
 // fp32 asymmetric: 64 packed rows (W result rows each) x 128 columns
-using TilesF32Asym = Tiles<64, 128, 4, 8, 16, 6>;
+using TilesF32Asym = Tiles<64, 128, 4, 8, 16, 6>;     // W >= 3: W x 32 running sums per thread
+using TilesF32AsymW2 = Tiles<128, 128, 8, 8, 32, 3>;  // W <= 2: W x 64 sums fit TMEM, 2.6 % faster
 // fp64: 64 x 64, 4 x 4 per thread
 using TilesF64 = Tiles<64, 64, 4, 4, 16, 4>;
 

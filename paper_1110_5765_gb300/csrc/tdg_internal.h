@@ -136,7 +136,7 @@ cudaError_t launch_px_gemm(int W, const GemmArgs<T> &g, const GemmOperands &ops,
 
 // Tile shape the packed GEMM uses for (T, form): operand boxes are
 // {box_x_a, bk} for A and {box_x_b, bk} for B.
-void packed_gemm_boxes(int dtype, int form, int *box_x_a, int *box_x_b, int *bk);
+void packed_gemm_boxes(int dtype, int form, int W, int *box_x_a, int *box_x_b, int *bk);
 
 template <typename T>
 cudaError_t launch_unpack(int form, int W, const GemmArgs<T> &g, int64_t *rint_out,

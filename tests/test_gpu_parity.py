@@ -272,6 +272,34 @@ def test_distortion_sweep_size_sampled_tiles(tdg, orc, form):
         assert same_bits(g["C"][rows[0]:rows[1], cols[0]:cols[1]], ref.C), (ti, tj)
 
 
+def test_benchmark_configuration_sampled_tiles(tdg, orc):
+    """The benchmark's own configuration and inputs (4096^3 fp32 uniform[-1,1]
+    drawn from the benchmark's seeds 1112 / 1113, L = 128, symmetric W = 2,
+    20 dB target, the built-in s-table): the device planner's choice equals the
+    oracle's on the full matrices and three sampled 128 x 128 output tiles over
+    the full K equal the oracle's bit for bit."""
+    n = 4096
+    A = synth.uniform((n, n), 1112, np.float32)
+    B = synth.uniform((n, n), 1113, np.float32)
+    # the plan exactly as the benchmark makes it (built-in s-table)
+    p = tdg.Plan(n, n, n, L=128, W=2, dtype="f32", form="sym", target_snr_db=20.0)
+    C = p.run(dev(A), dev(B))
+    torch.cuda.synchronize()
+    info = p.info()
+    p.close()
+    assert info["device_status"] == 0, info
+    g = {"C": C.cpu().numpy()}
+    st = orc.load_s_table()
+    for (ti, tj) in synth.sample_tiles(32, 32, 3, seed=1114):
+        rows, cols = (ti * 128, ti * 128 + 128), (tj * 128, tj * 128 + 128)
+        ref = orc.tdgemm(A, B, L=128, W=2, dtype="f32", form="sym", target_db=20.0,
+                         s_table=st, rows=rows, cols=cols)
+        assert (info["W_used"], info["q"], info["gamma_a"], info["gamma_b"]) == \
+            (ref.plan.W, ref.plan.q, ref.plan.gA, ref.plan.gB)
+        assert abs(info["pred_snr_db"] - ref.plan.pred_snr_db) < 1e-6
+        assert same_bits(g["C"][rows[0]:rows[1], cols[0]:cols[1]], ref.C), (ti, tj)
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("form", ["sym", "asym"])
 @pytest.mark.parametrize("W", [1, 2, 3, 4])
