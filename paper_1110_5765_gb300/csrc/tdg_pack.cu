@@ -215,6 +215,68 @@ __global__ void __launch_bounds__(256) pack_k_kc_kernel(Src<T> S, int P, const D
     }
 }
 
+// ------------------------------------------------------------------ plain k-major copy
+// out[k][x] = in[x][k] of a k-contiguous operand without companding (the
+// plain product's operands): 64 x 64 tiles through shared memory (s[x][k],
+// pitch 65), 16-byte loads along k issued before any is used, 16-byte stores
+// along x.  256 threads per CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_copy_kernel(Src<T> S, const DevPlan *plan,
+                                                             int expectW, T *out, long long ldo,
+                                                             int vec_ok) {
+    pdl_entry();
+    if (expectW > 0 && plan->W != expectW) return;
+    constexpr int VEC = VecT<T>::n;
+    constexpr int TT = 64, PITCH = TT + 1;
+    constexpr int NV = TT * TT / VEC / 256;     // vectors per thread and phase
+    __shared__ T s[TT * PITCH];
+    const long long xt = (S.X + TT - 1) / TT, kt = (S.K + TT - 1) / TT;
+    for (long long t = blockIdx.x; t < xt * kt; t += gridDim.x) {
+        const long long x0 = (t % xt) * TT, k0 = (t / xt) * TT;
+        T v[NV][VEC];
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+            const int e = threadIdx.x + u * 256;
+            const int xr = e / (TT / VEC), kc = (e % (TT / VEC)) * VEC;
+            const long long x = x0 + xr, k = k0 + kc;
+            if (x < S.X && vec_ok && k + VEC <= S.K) {
+                vload(S.p + x * S.sx + k, v[u]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q)
+                    v[u][q] = (x < S.X && k + q < S.K) ? S.p[x * S.sx + k + q] : T(0);
+            }
+        }
+        __syncthreads();   // the previous tile's readers are done with s
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+            const int e = threadIdx.x + u * 256;
+            const int xr = e / (TT / VEC), kc = (e % (TT / VEC)) * VEC;
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) s[xr * PITCH + kc + q] = v[u][q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+            const int e = threadIdx.x + u * 256;
+            const int kr = e / (TT / VEC), xc = (e % (TT / VEC)) * VEC;
+            const long long k = k0 + kr, x = x0 + xc;
+            if (k >= S.K || x >= S.X) continue;
+            T w[VEC];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) w[q] = s[(xc + q) * PITCH + kr];
+            T *dst = out + k * ldo + x;
+            if (vec_ok && x + VEC <= S.X) {
+                vstore(dst, w);
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q)
+                    if (x + q < S.X) dst[q] = w[q];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ pack along x
 // out[k][i*P + j] for j in [j0, j0 + 32) of row block i, k in [k0, k0 + 32)
 template <typename T, int W>
@@ -440,6 +502,12 @@ cudaError_t launch_pack_k_w(const PackOperand<T> &o, const DevPlan *plan, int ex
                                              (items + 255) / 256, 4)),
                           dim3(256), 0, st, S, P, plan, expectW, wsign, out, ldo, rows_out,
                           vec_ok);
+    } else if (W == 1 && o.c == nullptr && o.sk == 1 && rows_out == o.K) {
+        // plain copy: a straight transpose
+        const int vec_ok = aligned_in && aligned_out && (o.sx % VEC == 0);
+        const long long tiles = ((o.X + 63) / 64) * ((o.K + 63) / 64);
+        return launch_pdl(transpose_copy_kernel<T>, dim3(capped(tiles)), dim3(256), 0, st, S, plan,
+                          expectW, out, ldo, vec_ok);
     } else {
         const int vec_ok = aligned_in && (o.sx % VEC == 0) && o.sk == 1;
         const long long tiles = ((o.X + TILE - 1) / TILE) * ((o.K + o.L - 1) / o.L) *
