@@ -23,6 +23,13 @@ What it computes, with the passage each step follows (Anastasia & Andreopoulos,
 * ``exact_gemm``       fp64 reference product, ``snr_db`` (eq. 20 over all of C)
 * ``tc_int_gemm``      eq. 4 on exact integers per slab (the tensor-core form)
 * ``tc_fp8_gemm``      the same with 8-bit E4M3 codes instead of integers
+* ``kernel_ratios``    Sec. 6: predicted signal-to-noise ratio of every inner
+                       kernel (output block), eq. 21's terms summed over slabs
+* ``kernel_mask``      Sec. 6: the inner kernels accelerated under an SNR
+                       threshold or a fraction F of the best-predicted ones
+* ``pair_companders``, ``tdgemm_pair_exact``
+                       eq. 26 per subblock product (Prop. 4): each (i, l, j)
+                       pair's Gamma_A, Gamma_B split within the call's R_max
 
 Every function above is pinned to something outside itself (values printed
 in the paper, closed forms, library routines, brute force) in
