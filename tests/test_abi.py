@@ -80,4 +80,9 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.tdgemm_gemm(None, None, 1.0, 0.0, None) == 1
     assert lib.tdgemm_unpack(None, None, None, None) == 1
     assert lib.tdgemm_set_manual(None, 10, 1.0, 1.0) == 1
+    assert lib.tdgemm_set_kernel_control(None, 2, 0.5) == 1
+    assert lib.tdgemm_kernel_mask(None, None, 0) == 1
+    assert lib.tdgemm_quantize_pack_a(None, None, None) == 1
+    assert lib.tdgemm_run(None, None, None, None, 1.0, 0.0, None) == 1
+    assert lib.tdgemm_run_host(None, None, None, None, 1.0, 0.0, None) == 1
     assert lib.tdgemm_plan_destroy(None) == 0
