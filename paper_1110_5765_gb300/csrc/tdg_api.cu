@@ -689,7 +689,12 @@ extern "C" tdg_status tdgemm_run_host(tdgemm_plan_t p, const void *A, const void
     CU_TRY(cudaMemcpyAsync(p->hB, B, bbytes, cudaMemcpyHostToDevice, st));
     if (beta != 0.0) CU_TRY(cudaMemcpyAsync(p->hC, C, cbytes, cudaMemcpyHostToDevice, st));
     tdg_status r = tdgemm_run(p, p->hA, p->hB, c_direct ? c_direct : p->hC, alpha, beta, stream);
-    if (r != TDG_OK) return r;
+    if (r != TDG_OK) {
+        // the copies already queued read the caller's buffers: let them finish
+        // before the caller may reuse them
+        cudaStreamSynchronize(st);
+        return r;
+    }
     if (!c_direct) CU_TRY(cudaMemcpyAsync(C, p->hC, cbytes, cudaMemcpyDeviceToHost, st));
     CU_TRY(cudaStreamSynchronize(st));
     return TDG_OK;
