@@ -71,7 +71,7 @@ void orc_pack_cols_f32(const float *Xq, int64_t rows, int64_t cols, int L, int W
     for (int64_t r = 0; r < rows; ++r)
         for (int64_t l = 0; l < nb; ++l)
             for (int j = 0; j < P; ++j) {
-                float d[8];
+                float d[8] = {0};
                 for (int i = 0; i < W; ++i) {
                     int64_t inblk = (int64_t)W * j + i;
                     int64_t k = l * L + inblk;
@@ -91,7 +91,7 @@ void orc_pack_cols_f64(const double *Xq, int64_t rows, int64_t cols, int L, int 
     for (int64_t r = 0; r < rows; ++r)
         for (int64_t l = 0; l < nb; ++l)
             for (int j = 0; j < P; ++j) {
-                double d[8];
+                double d[8] = {0};
                 for (int i = 0; i < W; ++i) {
                     int64_t inblk = (int64_t)W * j + i;
                     int64_t k = l * L + inblk;
@@ -113,7 +113,7 @@ void orc_pack_rows_f32(const float *Xq, int64_t rows, int64_t cols, int L, int W
     for (int64_t l = 0; l < nb; ++l)
         for (int j = 0; j < P; ++j)
             for (int64_t c = 0; c < cols; ++c) {
-                float d[8];
+                float d[8] = {0};
                 for (int i = 0; i < W; ++i) {
                     int64_t inblk = (int64_t)W * j + i;
                     int64_t r = l * L + inblk;
@@ -133,7 +133,7 @@ void orc_pack_rows_f64(const double *Xq, int64_t rows, int64_t cols, int L, int 
     for (int64_t l = 0; l < nb; ++l)
         for (int j = 0; j < P; ++j)
             for (int64_t c = 0; c < cols; ++c) {
-                double d[8];
+                double d[8] = {0};
                 for (int i = 0; i < W; ++i) {
                     int64_t inblk = (int64_t)W * j + i;
                     int64_t r = l * L + inblk;
