@@ -127,7 +127,8 @@ typedef struct {
  *   dtype, form     see above
  *   target_snr_db   distortion target in dB (used when bits == 0)
  *   bits            > 0: fixed-bit companding, gamma = 2^(bits-1) - 1, W as
- *                   given (bits in 2..12; TC_INT up to 12)
+ *                   given (SYM, ASYM: bits in 2..20; TC_INT: 2..12 with
+ *                   L * gamma^2 below 2^24)
  *   flags           TDG_ALLOW_FALLBACK | TDG_KEEP_PACKED | TDG_NOISE_RMS |
  *                   TDG_PAIR_EXACT
  *
@@ -266,12 +267,16 @@ tdg_status tdgemm_snr(const void *C, int64_t ldc, tdg_dtype dtype, const double 
  * with the statistics, companders, de-companding factors and packed operands
  * in one static device array of 32 MiB that the library holds on every GPU
  * that loads it, instead of plan workspace from cudaMalloc.  For callers that
- * may not allocate device memory where they call: code running while a stream
- * is captured into a CUDA graph, allocators that own the whole device, and
- * latency-bound services that must not allocate on first use.
+ * may not allocate device memory where they call: frameworks whose allocator
+ * owns the whole device and forbids libraries' side allocations, plug-ins
+ * handed only the buffers they compute on, and latency-bound services that
+ * must not allocate (or synchronise the device) on first use.
  *   form     TDG_SYM or TDG_ASYM; W 1..4; bits 2..20 (gamma = 2^(bits-1) - 1);
  *            other arguments as in tdgemm_plan / tdgemm_gemm.  A, B, C device.
  * Results equal those of tdgemm_plan + tdgemm_run with the same arguments.
+ * Device-side conditions are not reported: a NaN or Inf in A or B leaves
+ * non-finite values in C and the call still returns TDG_OK (the plan-based
+ * path reports it through tdgemm_plan_info).  M, N, K <= 2^31.
  * A product whose workspace exceeds the 32 MiB is rejected with TDG_EINVAL
  * before any device work.  Every call reuses the same array (it keeps the
  * previous call's contents; each call clears what must start at zero), so

@@ -23,6 +23,8 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <mutex>
+
 #include "tdg_common.cuh"
 #include "tdg_internal.h"
 
@@ -461,27 +463,31 @@ Src<T> make_src(const PackOperand<T> &o) {
 int capped(long long n) { return (int)max(1LL, min(n, (long long)MAX_CTAS)); }
 
 // Grid of at most `waves` full waves of resident CTAs for `kern` (occupancy
-// x SMs, cached per kernel), so a grid-stride kernel never ends on a partial
-// wave of long-running CTAs and an early exit costs few CTAs.
+// x SMs, cached per device and kernel under a lock, since host threads may
+// launch concurrently), so a grid-stride kernel never ends on a partial wave
+// of long-running CTAs and an early exit costs few CTAs.
 int resident_grid(const void *kern, long long n, int waves) {
-    struct Entry { const void *k; int ctas; };
-    static Entry cache[64];
-    static int ncache = 0, sms = 0;
+    struct Entry { const void *k; int dev, ctas; };
+    static Entry cache[128];
+    static int ncache = 0;
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
     int ctas = 0;
-    for (int i = 0; i < ncache; ++i)
-        if (cache[i].k == kern) ctas = cache[i].ctas;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (int i = 0; i < ncache; ++i)
+            if (cache[i].k == kern && cache[i].dev == dev) ctas = cache[i].ctas;
+    }
     if (!ctas) {
-        if (!sms) {
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (sms <= 0) sms = 152;
-        }
-        int per = 0;
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0) != cudaSuccess || per < 1)
             per = 1;
         ctas = per * sms;
-        if (ncache < 64) cache[ncache++] = {kern, ctas};
+        std::lock_guard<std::mutex> lock(mu);
+        if (ncache < 128) cache[ncache++] = {kern, dev, ctas};
     }
     return (int)max(1LL, min(n, (long long)ctas * waves));
 }

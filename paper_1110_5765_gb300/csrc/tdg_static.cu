@@ -3,12 +3,16 @@
 // cudaMalloc.
 //
 // Who needs it: callers that may not allocate device memory at the point of
-// the call — code running while a stream is being captured into a CUDA graph
-// (allocation is not a capturable operation), allocators that own the whole
-// device and forbid side allocations, and services that must not take a
-// first-use allocation latency on a hot path.  They pass A, B and C; the
-// statistics, companders, de-companding factors and packed operands live in
-// g_scratch below.
+// the call — frameworks whose allocator owns the whole device and forbids side
+// allocations by libraries, plug-ins that are handed only the buffers they
+// compute on, and services that must not take a first-use allocation (and the
+// device-wide synchronisation cudaMalloc/cudaFree can imply) on a hot path.
+// They pass A, B and C; the statistics, companders, de-companding factors and
+// packed operands live in g_scratch below.
+//
+// Unlike the plan-based path, nothing reports device-side conditions back: a
+// NaN or Inf in A or B is flagged in the plan record inside g_scratch, which
+// no entry point reads, and C then holds non-finite values.
 //
 // Limits and sharing:
 //   * g_scratch holds kStaticScratchBytes (32 MiB) on every GPU that loads the
@@ -175,6 +179,10 @@ extern "C" tdg_status tdgemm_run_static(char transA, char transB, int64_t M, int
     auto okT = [](char t) { return t == 'N' || t == 'n' || t == 'T' || t == 't'; };
     if (!okT(transA) || !okT(transB)) return err(TDG_EINVAL, "trans must be 'N' or 'T'");
     if (M < 1 || N < 1 || K < 1) return err(TDG_EINVAL, "M, N, K must be >= 1");
+    // the block counts and tile coordinates are 32-bit: sizes beyond 2^31 would
+    // wrap them and with them the scratch layout
+    if (M > (1LL << 31) || N > (1LL << 31) || K > (1LL << 31))
+        return err(TDG_EINVAL, "M, N, K must be <= 2^31");
     const bool nA = transA == 'N' || transA == 'n', nB = transB == 'N' || transB == 'n';
     if (lda < (nA ? K : M) || ldb < (nB ? N : K) || ldc < N)
         return err(TDG_EINVAL, "leading dimension too small");

@@ -145,7 +145,7 @@ def test_2dpca_recognition_at_20db(tdg, orc, faces2d):
     noise): the planner packs all three at W = 2, recognition stays within two
     test images of the exact fp64 pipeline, and G is bit-identical to the
     oracle's; the paper's ad-hoc parameters (W = 2, R_max = 50000, c = 0.1)
-    wreck it (P:451's 44 %)."""
+    wreck it (Sec. 8.A, Table 1: 44 %)."""
     acc_exact, _ = _2dpca(faces2d, lambda a, b, _: a.astype(np.float64) @ b.astype(np.float64))
     plans = {}
 
