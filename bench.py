@@ -52,7 +52,6 @@ WORKLOAD = ("distortion sweep point: C = A B, M = N = K = 4096, fp32 inputs iid 
             "block L = 128, per-block adaptive companding, symmetric packing W = 2, "
             "target 20 dB")
 FP32_LANES_PER_SM = 128
-NUM_SMS = 152
 
 
 def peaks():
@@ -299,18 +298,23 @@ def run_gpu(args):
 
     # ---- roofline of the packed GEMM kernel (FP32 FMA pipe)
     pk, src = peaks()
+    probe = fma_peaks(tdg, torch)
     W_used = max(1, info["W_used"])
     P = -(-L_BLOCK // W_used)
     Kp = (K // L_BLOCK) * P if W_used > 1 else K
     gemm_flops = 2.0 * M * N * Kp                        # algorithmic: 2 M N K / W
     gemm_s = statistics.mean(gemm_ms) / 1e3
-    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
+    sms = probe["sms"]
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
     achieved = gemm_flops / gemm_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": gemm_traffic(W_used),
                 "kernel": f"packed_gemm_kernel<float, {'SYM' if W_used > 1 else 'PLAIN'}, W={W_used}> (FP32 FMA pipe)",
-                "peak_source": (f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz "
+                "peak_source": (f"{sms} SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz "
                                 "(unit counts and maximum SM clock)"),
+                "peak_probe": probe["f32_tflops"],
+                "frac_of_probe": achieved / probe["f32_tflops"],
+                "probe_source": "tdgemm_fma_probe: fma.rn.f32x2 chains on every SM, CUDA events",
                 "work_per_launch": f"2 M N K / W flops = {gemm_flops:.3e}"}
 
     # ---- end to end through the host-buffer entry point
@@ -361,8 +365,14 @@ def run_gpu(args):
                 "peaks_source": src}
         if cpu is not None:
             line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["fma_peaks"] = {"f32_tflops": probe["f32_tflops"], "f64_tflops": probe["f64_tflops"],
+                             "sms": sms}
         if forms:
             line["forms"] = forms
+            # compact per-form rooflines, printed last so the end of the line shows them
+            line["rooflines"] = rooflines(forms, {"f32_tflops": probe["f32_tflops"],
+                                                  "f64_tflops": probe["f64_tflops"],
+                                                  "bf16_tflops": pk["bf16_tflops"]})
         print(json.dumps(line))
     plan.close()
     if world > 1:
@@ -414,6 +424,113 @@ def _time(fn, torch, reps=3):
     return s0.elapsed_time(s1) / 1e3 / reps
 
 
+def fma_peaks(tdg, torch) -> dict:
+    """FP32 / FP64 FMA-pipe peaks measured on this GPU (tdgemm_fma_probe:
+    independent fma.rn.f32x2 / fma.rn.f64 chains on every SM, no memory),
+    best of three CUDA-event-timed launches, and the SM count from the
+    device's properties."""
+    out = {"sms": torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count}
+    for dt, iters in (("f32", 20000), ("f64", 400)):
+        tdg.fma_probe(dt, max(1, iters // 10))
+        torch.cuda.synchronize()
+        best = 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fl = tdg.fma_probe(dt, iters)
+            e1.record()
+            torch.cuda.synchronize()
+            best = max(best, fl / (e0.elapsed_time(e1) / 1e3))
+        out[f"{dt}_tflops"] = best / 1e12
+    return out
+
+
+def _time_split(p, A, B, C, torch, reps=3):
+    """Whole path and GEMM step (tdgemm_gemm alone) per call, CUDA events on
+    the launching stream, after one warm-up call."""
+    p.run(A, B, C)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(reps)]
+    for e0, e1, e2 in ev:
+        e0.record()
+        p.quantize_pack(A, B)
+        e1.record()
+        p.gemm(C)
+        e2.record()
+    torch.cuda.synchronize()
+    t = statistics.mean(a.elapsed_time(c) for a, _, c in ev) / 1e3
+    tg = statistics.mean(b.elapsed_time(c) for _, b, c in ev) / 1e3
+    return t, tg
+
+
+def kernel_work(form: str, W: int, M: int, N: int, K: int, L: int) -> float:
+    """Algorithmic flops of the GEMM kernel of one call: 2 per fused
+    multiply-add the packed (or plain, or tensor-core) main loop performs:
+    sym M x N x nK ceil(L/W), asym nM ceil(L/W) x N x K, plain and tensor-core
+    forms M x N x K."""
+    nM, nK = -(-M // L), -(-K // L)
+    P = -(-L // W)
+    if form == "sym" and W > 1:
+        return 2.0 * M * N * nK * P
+    if form == "asym" and W > 1:
+        return 2.0 * nM * P * N * K
+    return 2.0 * M * N * K
+
+
+def roofline_entry(rec: dict, form: str, dtype: str, M: int, N: int, K: int, pk: dict) -> dict:
+    """Compact per-form roofline: whole-path effective TFLOP/s, SNR, W used,
+    the GEMM kernel's algorithmic TFLOP/s and its fraction of the pipe it runs
+    on (FP32 / FP64 FMA probe, tensor pipe: measured bf16 burst, x2 for E4M3)."""
+    W = int(rec.get("W_used", 1) or 1)
+    fam = form if W > 1 or form.startswith("tc") else "plain"
+    if form == "tc_fp8":
+        peak, src = 2.0 * pk["bf16_tflops"], "tc8"
+    elif form == "tc_int":
+        peak, src = pk["bf16_tflops"], "tc16"
+    else:
+        peak, src = pk[f"{dtype}_tflops"], dtype
+    e = {"T": round(rec["gflops"] / 1e3, 2), "dB": round(rec["snr_db"], 1), "W": W}
+    if "gemm_ms" in rec:
+        kt = kernel_work(fam, W, M, N, K, L_BLOCK) / (rec["gemm_ms"] / 1e3) / 1e12
+        e.update({"kT": round(kt, 2), "f": round(kt / peak, 3), "pk": src})
+    return e
+
+
+ROOFLINE_FORMS = [
+    # (key in forms, form, dtype, size)
+    ("cublas_f32", "cublas", "f32", 4096), ("cublas_f64", "cublas", "f64", 4096),
+    ("plain_f32", "plain", "f32", 4096), ("plain_f64", "plain", "f64", 4096),
+    ("sym_f32_W2_20dB", "sym", "f32", 4096), ("asym_f32_W2_20dB", "asym", "f32", 4096),
+    ("sym_f32_W2_40dB", "sym", "f32", 4096), ("asym_f32_W2_40dB", "asym", "f32", 4096),
+    ("sym_f64_W2_40dB", "sym", "f64", 4096), ("sym_f64_W3_40dB", "sym", "f64", 4096),
+    ("asym_f64_W2_40dB", "asym", "f64", 4096), ("asym_f64_W3_40dB", "asym", "f64", 4096),
+    ("tc_int_40dB", "tc_int", "f32", 4096), ("tc_fp8", "tc_fp8", "f32", 4096),
+    ("p8192_cublas_f32", "cublas", "f32", 8192),
+    ("p8192_sym_f32_W2_40dB", "sym", "f32", 8192), ("p8192_sym_f64_W3_40dB", "sym", "f64", 8192),
+    ("p8192_asym_f64_W3_40dB", "asym", "f64", 8192),
+    ("p8192_tc_int_40dB", "tc_int", "f32", 8192), ("p8192_tc_fp8", "tc_fp8", "f32", 8192),
+]
+
+
+def rooflines(forms: dict, pk: dict) -> dict:
+    """Per-form rooflines of the spec comparison (4096^3 uniform, 8192^3
+    Laplacian; 40 dB targets, 20 dB where fp32 packing engages)."""
+    out = {"_": ("T: whole-path effective TFLOP/s (2MNK/t); dB: SNR vs fp64; W: packing used; "
+                 "kT: GEMM kernel algorithmic TFLOP/s (2 per FMA it performs); f = kT / peak; "
+                 f"pk: f32 = {pk['f32_tflops']:.1f}, f64 = {pk['f64_tflops']:.2f} TFLOP/s "
+                 "(FMA probe, measured), tc16 = measured bf16 burst "
+                 f"{pk['bf16_tflops']:.0f}, tc8 = 2 x that")}
+    for key, form, dtype, n in ROOFLINE_FORMS:
+        rec = forms.get(key)
+        if not rec or "gflops" not in rec:
+            continue
+        if form == "cublas":
+            rec = dict(rec, gemm_ms=rec["ms"], W_used=1)
+            form = "plain"
+        out[key.replace("p8192_", "8k_")] = roofline_entry(rec, form, dtype, n, n, n, pk)
+    return out
+
+
 def measure_forms(tdg, torch, A32, B32) -> dict:
     """Every form at 4096^3 beside plain fp32/fp64 GEMM on the same GPU:
     effective GFLOP/s (whole path) and SNR against the fp64 product."""
@@ -442,8 +559,10 @@ def measure_forms(tdg, torch, A32, B32) -> dict:
         ("sym_f32_W2_20dB_pair_exact", dict(dtype="f32", form="sym", W=2, target_snr_db=20.0,
                                             pair_exact=True), A32, B32),
         ("sym_f32_W2_40dB", dict(dtype="f32", form="sym", W=2, target_snr_db=40.0), A32, B32),
+        ("asym_f32_W2_40dB", dict(dtype="f32", form="asym", W=2, target_snr_db=40.0), A32, B32),
         ("sym_f64_W2_40dB", dict(dtype="f64", form="sym", W=2, target_snr_db=40.0), A64, B64),
         ("sym_f64_W3_40dB", dict(dtype="f64", form="sym", W=3, target_snr_db=40.0), A64, B64),
+        ("asym_f64_W2_40dB", dict(dtype="f64", form="asym", W=2, target_snr_db=40.0), A64, B64),
         ("asym_f64_W3_40dB", dict(dtype="f64", form="asym", W=3, target_snr_db=40.0), A64, B64),
         ("sym_f64_W4_20dB", dict(dtype="f64", form="sym", W=4, target_snr_db=20.0), A64, B64),
         ("tc_int_8bit", dict(dtype="f32", form="tc_int", W=1, bits=8), A32, B32),
@@ -457,9 +576,10 @@ def measure_forms(tdg, torch, A32, B32) -> dict:
             p = tdg.Plan(n, n, n, L=L_BLOCK, **kw)
             C = C64 if kw["dtype"] == "f64" and not kw["form"].startswith("tc") else C32
             reps = 1 if kw["dtype"] == "f64" else 3
-            t = _time(lambda: p.run(A, B, C), torch, reps=reps)
+            t, tg = _time_split(p, A, B, C, torch, reps=reps)
             info = p.info()
-            rec(name, t, C, {"W_used": info["W_used"], "pred_snr_db": info["pred_snr_db"]})
+            rec(name, t, C, {"W_used": info["W_used"], "pred_snr_db": info["pred_snr_db"],
+                             "gemm_ms": tg * 1e3})
             p.close()
         except Exception as e:     # a form not built yet is reported, not hidden
             out[name] = {"error": str(e)[:200]}
@@ -973,11 +1093,12 @@ def measure_precision_form(tdg, torch) -> dict:
     for name, kw in cases:
         try:
             p = tdg.Plan(n, n, n, L=L_BLOCK, dtype="f32", **kw)
-            t = _time(lambda: p.run(A, B, C32), torch)
+            t, tg = _time_split(p, A, B, C32, torch)
             info = p.info()
             out[name] = {"gflops": flops / t / 1e9, "ms": t * 1e3, "snr_db": tdg.snr_db(C32, ref),
                          "W_used": info["W_used"], "pred_snr_db": info["pred_snr_db"],
-                         "gamma_a": info["gamma_a"], "gamma_b": info["gamma_b"]}
+                         "gamma_a": info["gamma_a"], "gamma_b": info["gamma_b"],
+                         "gemm_ms": tg * 1e3}
             p.close()
         except Exception as e:
             out[name] = {"error": str(e)[:200]}
@@ -985,13 +1106,14 @@ def measure_precision_form(tdg, torch) -> dict:
     C64 = torch.empty_like(A64)
     t = _time(lambda: torch.matmul(A64, B64, out=C64), torch, reps=1)
     out["p8192_cublas_f64"] = {"gflops": flops / t / 1e9, "ms": t * 1e3}
-    p = tdg.Plan(n, n, n, L=L_BLOCK, dtype="f64", form="sym", W=3, target_snr_db=40.0)
-    t = _time(lambda: p.run(A64, B64, C64), torch, reps=1)
-    info = p.info()
-    out["p8192_sym_f64_W3_40dB"] = {"gflops": flops / t / 1e9, "ms": t * 1e3,
-                                   "snr_db": tdg.snr_db(C64, ref), "W_used": info["W_used"],
-                                   "pred_snr_db": info["pred_snr_db"]}
-    p.close()
+    for form in ("sym", "asym"):
+        p = tdg.Plan(n, n, n, L=L_BLOCK, dtype="f64", form=form, W=3, target_snr_db=40.0)
+        t, tg = _time_split(p, A64, B64, C64, torch, reps=1)
+        info = p.info()
+        out[f"p8192_{form}_f64_W3_40dB"] = {"gflops": flops / t / 1e9, "ms": t * 1e3,
+                                           "snr_db": tdg.snr_db(C64, ref), "W_used": info["W_used"],
+                                           "pred_snr_db": info["pred_snr_db"], "gemm_ms": tg * 1e3}
+        p.close()
     return out
 
 

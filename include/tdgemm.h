@@ -91,12 +91,18 @@ typedef enum {
                                     transB = 'N', L = 128 (fp32) or 64 (fp64), W
                                     in {2, 4} (target mode: W = 2); each CTA then
                                     compands and packs its own operand tiles      */
-#define TDG_NOISE_RMS      0x4u  /* planner: scale the measured representation
-                                    noise s(R_max, W) (taken with uniform integer
-                                    inputs, Sec. 4.B) by 3 kappa_A kappa_B, the
-                                    blocks' crest factors kappa = sigma / max; a
-                                    refinement beyond the paper for peaky
-                                    sources (uniform sources: no change)        */
+#define TDG_NOISE_RMS      0x4u  /* planner: the representation noise s(R_max, W),
+                                    measured with uniform integer inputs (Sec. 4.B),
+                                    scaled by 3 kappa_A kappa_B, the blocks' crest
+                                    factors kappa = sigma / max (the rounding error
+                                    of the packed sums follows their RMS).  The
+                                    default; the flag is accepted and changes
+                                    nothing.  Uniform sources: no change.        */
+#define TDG_NOISE_UNIFORM  0x10u /* planner: s(R_max, W) as measured, unscaled
+                                    (the paper's model of eq. 21 with the Sec. 4.B
+                                    calibration as it stands); pessimistic by
+                                    several dB for peaky (Gaussian, Laplacian)
+                                    sources.  Not with TDG_NOISE_RMS.            */
 
 /* What the planner chose, read back by tdgemm_plan_info (synchronises). */
 typedef struct {
@@ -130,7 +136,7 @@ typedef struct {
  *                   given (SYM, ASYM: bits in 2..20; TC_INT: 2..12 with
  *                   L * gamma^2 below 2^24)
  *   flags           TDG_ALLOW_FALLBACK | TDG_KEEP_PACKED | TDG_NOISE_RMS |
- *                   TDG_PAIR_EXACT
+ *                   TDG_NOISE_UNIFORM | TDG_PAIR_EXACT
  *
  * On success *plan receives a new plan holding all device workspace for these
  * shapes (allocated on the current device).  On error *plan is left NULL.
@@ -289,6 +295,31 @@ tdg_status tdgemm_run_static(char transA, char transB, int64_t M, int64_t N, int
                              int64_t lda, int64_t ldb, int64_t ldc, int L, int W,
                              tdg_dtype dtype, tdg_form form, int bits, const void *A,
                              const void *B, void *C, double alpha, double beta, void *stream);
+
+/*
+ * Test of the device-side failure path (the library's own, not the paper's):
+ * every device wait is bounded and, when its limit passes, the kernel records
+ * TDG_ETIMEOUT, lets the copies it issued land, frees what it holds and
+ * returns.  With limit_ns > 0, every later tdgemm_gemm of this plan makes the
+ * CUDA-core GEMM kernel's first wait for its operand tiles wait instead on a
+ * barrier that nothing completes, for limit_ns nanoseconds; the kernel then
+ * takes that path, tdgemm_plan_info reports device_status TDG_ETIMEOUT, and
+ * C is left unspecified.  The next tdgemm_quantize_pack clears the status.
+ * 0 turns the test off.  PLAIN, SYM and ASYM forms without TDG_PAIR_EXACT;
+ * limit_ns in [0, 1e9]; TDG_EINVAL otherwise.
+ */
+tdg_status tdgemm_set_wait_test(tdgemm_plan_t plan, int64_t limit_ns);
+
+/*
+ * Measurement aid for the roofline of the CUDA-core forms (not part of the
+ * paper's method): one launch of independent fused multiply-add chains on
+ * every SM, no memory traffic, on `stream` (asynchronous; time it with
+ * events around the call).  dtype TDG_F32 runs the packed fma.rn.f32x2 the
+ * fp32 GEMM uses, TDG_F64 scalar fma.rn.f64.  iters >= 1 chain steps per
+ * thread; *flops (host) receives the floating-point operations the launch
+ * performs (2 per fused multiply-add).
+ */
+tdg_status tdgemm_fma_probe(tdg_dtype dtype, int64_t iters, double *flops, void *stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *tdgemm_last_error(void);

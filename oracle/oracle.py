@@ -595,7 +595,7 @@ class Result:
 def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: str,
            bits: int = 0, target_db: float = math.nan, s_table: STable | None = None,
            allow_fallback: bool = True, manual: tuple | None = None,
-           gammas: tuple | None = None, noise_rms: bool = False,
+           gammas: tuple | None = None, noise_rms: bool = True,
            alpha: float = 1.0, beta: float = 0.0, C_in: np.ndarray | None = None,
            rows=None, cols=None, want_rint: bool = False, keep_packed: bool = False,
            kernel_control: tuple | None = None) -> Result:
@@ -606,8 +606,9 @@ def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: st
     Parameters come from ``bits`` (fixed-bit mode), ``target_db`` (distortion
     target) or ``manual = (q, c_A, c_B)`` (uniform companders, as in the
     measurement protocol of Sec. 4.B) or ``gammas = (Gamma_A, Gamma_B)``
-    (given integer companders).  ``noise_rms`` selects the RMS-scaled
-    representation noise of ``model_noise``.  ``kernel_control = (mode,
+    (given integer companders).  ``noise_rms`` (the default) selects the
+    RMS-scaled representation noise of ``model_noise``; False takes s as
+    calibrated on uniform integers, unscaled.  ``kernel_control = (mode,
     value)`` ('snr' or 'fraction', Sec. 6) computes the inner kernels that
     ``kernel_mask`` leaves out with the conventional product instead.  ``rows``/``cols`` restrict the computed
     outputs to a window (for asym, row windows must align to L)."""

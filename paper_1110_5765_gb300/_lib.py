@@ -19,6 +19,7 @@ TDG_ALLOW_FALLBACK = 0x1
 TDG_KEEP_PACKED = 0x2
 TDG_NOISE_RMS = 0x4
 TDG_PAIR_EXACT = 0x8
+TDG_NOISE_UNIFORM = 0x10
 STATUS = {0: "TDG_OK", 1: "TDG_EINVAL", 2: "TDG_ENOMEM", 3: "TDG_ECUDA", 4: "TDG_EUNSUPPORTED",
           5: "TDG_EUNREACHABLE", 6: "TDG_ETIMEOUT", 7: "TDG_ENONFINITE", 8: "TDG_ESTATE"}
 
@@ -27,8 +28,8 @@ EXPORTS = ["tdgemm_plan", "tdgemm_set_rep_noise", "tdgemm_set_manual",
            "tdgemm_set_kernel_control", "tdgemm_kernel_mask", "tdgemm_quantize_pack",
            "tdgemm_quantize_pack_a",
            "tdgemm_gemm", "tdgemm_run", "tdgemm_run_host", "tdgemm_unpack", "tdgemm_plan_info",
-           "tdgemm_plan_destroy", "tdgemm_snr", "tdgemm_run_static", "tdgemm_last_error",
-           "tdgemm_version"]
+           "tdgemm_plan_destroy", "tdgemm_snr", "tdgemm_run_static", "tdgemm_set_wait_test",
+           "tdgemm_fma_probe", "tdgemm_last_error", "tdgemm_version"]
 
 
 class Info(ctypes.Structure):
@@ -74,6 +75,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.tdgemm_snr.argtypes = [vp, i64, i32, vp, i64, i64, i64, vp, vp]
     L.tdgemm_run_static.argtypes = [ctypes.c_char, ctypes.c_char, i64, i64, i64, i64, i64, i64,
                                     i32, i32, i32, i32, i32, vp, vp, vp, dbl, dbl, vp]
+    L.tdgemm_set_wait_test.argtypes = [vp, i64]
+    L.tdgemm_fma_probe.argtypes = [i32, i64, ctypes.POINTER(dbl), vp]
     L.tdgemm_last_error.restype = ctypes.c_char_p
     L.tdgemm_version.restype = ctypes.c_char_p
     for name in EXPORTS:

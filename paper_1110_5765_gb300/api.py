@@ -17,7 +17,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (DTYPES, FORMS, TDG_ALLOW_FALLBACK, TDG_KEEP_PACKED, TDG_NOISE_RMS,
+from ._lib import (DTYPES, FORMS, TDG_ALLOW_FALLBACK, TDG_KEEP_PACKED, TDG_NOISE_UNIFORM,
                    TDG_PAIR_EXACT, Info, check)
 
 _TORCH_DT = {"f32": torch.float32, "f64": torch.float64}
@@ -83,7 +83,9 @@ class Plan:
 
     form: 'plain' | 'sym' | 'asym' | 'tc_int' | 'tc_fp8'
     Parameters follow the paper: block size L, packing W, and either a
-    distortion target (dB) or fixed bits.
+    distortion target (dB) or fixed bits.  ``noise_rms=False`` plans with the
+    representation noise as calibrated on uniform integers, unscaled
+    (TDG_NOISE_UNIFORM); the default scales it by the blocks' crest factors.
     """
 
     def __init__(self, M: int, N: int, K: int, *, L: int = 128, W: int = 2, dtype: str = "f32",
@@ -91,7 +93,7 @@ class Plan:
                  transA: str = "N", transB: str = "N", lda: int | None = None,
                  ldb: int | None = None, ldc: int | None = None, allow_fallback: bool = True,
                  keep_packed: bool = False, rep_noise: str | dict | None = "package",
-                 noise_rms: bool = False, pair_exact: bool = False):
+                 noise_rms: bool = True, pair_exact: bool = False):
         self._L = _lib.load()
         self.M, self.N, self.K = int(M), int(N), int(K)
         self.L, self.W, self.dtype, self.form = int(L), int(W), dtype, form
@@ -100,7 +102,7 @@ class Plan:
         self.ldb = ldb if ldb is not None else (self.N if transB == "N" else self.K)
         self.ldc = ldc if ldc is not None else self.N
         flags = ((TDG_ALLOW_FALLBACK if allow_fallback else 0) | (TDG_KEEP_PACKED if keep_packed else 0)
-                 | (TDG_NOISE_RMS if noise_rms else 0) | (TDG_PAIR_EXACT if pair_exact else 0))
+                 | (0 if noise_rms else TDG_NOISE_UNIFORM) | (TDG_PAIR_EXACT if pair_exact else 0))
         h = ctypes.c_void_p()
         check(self._L.tdgemm_plan(ctypes.byref(h), transA.encode(), transB.encode(), self.M,
                                   self.N, self.K, self.lda, self.ldb, self.ldc, self.L, self.W,
@@ -132,6 +134,12 @@ class Plan:
         the ``ceil(value * nM * nN)`` blocks of highest predicted SNR; the
         others are computed with the conventional product.  None turns it off."""
         check(self._L.tdgemm_set_kernel_control(self._h, self._KCTRL[mode], float(value)))
+
+    def set_wait_test(self, limit_ns: int):
+        """Test of the bounded device waits: > 0 makes the next GEMMs' first
+        wait for operand tiles run out after ``limit_ns`` and report
+        TDG_ETIMEOUT in ``info()['device_status']``; 0 turns it off."""
+        check(self._L.tdgemm_set_wait_test(self._h, int(limit_ns)))
 
     def kernel_mask(self) -> np.ndarray:
         """(nM, nN) uint8 mask of the inner kernels the last pack accelerated."""
@@ -228,6 +236,16 @@ def tdgemm(A: torch.Tensor, B: torch.Tensor, *, alpha: float = 1.0, beta: float 
         out = p.run(A.t() if tA == "T" else A, B.t() if tB == "T" else B, C, alpha, beta)
         torch.cuda.current_stream().synchronize()
     return out
+
+
+def fma_probe(dtype: str, iters: int, stream=None) -> float:
+    """Queue one launch of independent FMA chains on every SM (FP32 pipe
+    through fma.rn.f32x2, or FP64); returns the flops it performs.  Time it
+    with CUDA events around the call."""
+    L = _lib.load()
+    fl = ctypes.c_double()
+    check(L.tdgemm_fma_probe(DTYPES[dtype], int(iters), ctypes.byref(fl), _stream_ptr(stream)))
+    return fl.value
 
 
 def snr_sums(C: torch.Tensor, ref: torch.Tensor, stream=None) -> tuple[float, float, float]:

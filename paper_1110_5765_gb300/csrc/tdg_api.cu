@@ -94,6 +94,7 @@ struct tdgemm_plan_s {
     const void *A_user = nullptr, *B_user = nullptr;
     bool packed = false, gemm_done = false, b_packed = false;
     int split_groups = 1;   // slab splitting of the packed GEMM (> 1: on)
+    long long stall_ns = 0; // test of the bounded waits (tdgemm_set_wait_test)
     int last_pack_W = 0;
     cudaStream_t last_stream = nullptr;
     int device = 0;
@@ -192,6 +193,8 @@ extern "C" tdg_status tdgemm_plan(tdgemm_plan_t *plan, char transA, char transB,
     tdg_status v = validate(transA, transB, M, N, K, lda, ldb, ldc, L, W, dtype, form,
                             target_snr_db, bits);
     if (v != TDG_OK) return v;
+    if ((flags & TDG_NOISE_RMS) && (flags & TDG_NOISE_UNIFORM))
+        return fail(TDG_EINVAL, "TDG_NOISE_RMS and TDG_NOISE_UNIFORM exclude each other");
     if (flags & TDG_PAIR_EXACT) {
         const bool tn = (transA == 'N' || transA == 'n') && (transB == 'N' || transB == 'n');
         if (form != TDG_SYM || !tn)
@@ -378,6 +381,18 @@ extern "C" tdg_status tdgemm_set_kernel_control(tdgemm_plan_t p, int mode, doubl
     return TDG_OK;
 }
 
+extern "C" tdg_status tdgemm_set_wait_test(tdgemm_plan_t p, int64_t limit_ns) {
+    if (!p) return fail(TDG_EINVAL, "plan is NULL");
+    if (!(is_packed_form(p->form) || p->form == TDG_PLAIN) || (p->flags & TDG_PAIR_EXACT))
+        return fail(TDG_EINVAL,
+                    "the wait test covers the CUDA-core GEMM (PLAIN, SYM, ASYM without "
+                    "TDG_PAIR_EXACT)");
+    if (limit_ns < 0 || limit_ns > 1000000000LL)
+        return fail(TDG_EINVAL, "limit_ns must be in [0, 1e9]");
+    p->stall_ns = limit_ns;
+    return TDG_OK;
+}
+
 extern "C" tdg_status tdgemm_kernel_mask(tdgemm_plan_t p, uint8_t *out, int64_t n) {
     if (!p || !out) return fail(TDG_EINVAL, "NULL argument");
     const long long T = (long long)p->nM * p->nN;
@@ -396,7 +411,7 @@ static PlanParams params_of(const tdgemm_plan_s *p) {
     if (is_tc_form(p->form)) pp.p = 24;
     pp.bits = p->bits;
     pp.allow_fallback = (p->flags & TDG_ALLOW_FALLBACK) ? 1 : 0;
-    pp.noise_rms = (p->flags & TDG_NOISE_RMS) ? 1 : 0;
+    pp.noise_rms = (p->flags & TDG_NOISE_UNIFORM) ? 0 : 1;
     pp.target_db = p->target;
     pp.manual_q = p->manual_q; pp.manual_cA = p->manual_cA; pp.manual_cB = p->manual_cB;
     pp.nM = p->nM; pp.nK = p->nK; pp.nN = p->nN;
@@ -578,6 +593,7 @@ static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cu
         g.C = C; g.ldc = p->ldc;
         g.alpha = (T)alpha; g.beta = (T)beta; g.beta_zero = beta == 0.0;
         g.Rbar = (!plain && (p->flags & TDG_KEEP_PACKED)) ? (T *)p->Rbar : nullptr;
+        g.stall_ns = p->stall_ns;
         const bool split = !plain && p->split_groups > 1 && !p->kctrl_mode && p->Rbar;
         if (split) {
             g.Rbar = (T *)p->Rbar;

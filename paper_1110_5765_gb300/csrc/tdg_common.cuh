@@ -177,6 +177,16 @@ __device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
     }
 }
 
+// bounded wait with its own budget (the test of the waits' expiry path)
+__device__ inline bool mbar_wait_ns(uint64_t *bar, uint32_t parity, uint64_t budget_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t start = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - start > budget_ns) return false;
+    }
+}
+
 // bounded wait whose retries (and, with first_too, its first test) may
 // suspend the thread for up to 1 ms each
 __device__ inline bool mbar_wait_bounded_suspend(uint64_t *bar, uint32_t parity,

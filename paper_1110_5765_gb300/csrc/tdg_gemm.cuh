@@ -247,6 +247,9 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
     T *sB = reinterpret_cast<T *>(smem + STAGES * Cfg::STAGE_A);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * (Cfg::STAGE_A + Cfg::STAGE_B));
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(full + STAGES);
+    // the test of the waits' expiry path waits on this barrier, which nothing
+    // completes (the second 8 bytes after the ring's barriers)
+    uint64_t *never = full + STAGES + 1;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -273,6 +276,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
     if (TMEMC && warp == 0) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        if (g.stall_ns > 0) mbar_init(never, 1);
         fence_barrier_init();
         tma_prefetch_desc(mA);
         tma_prefetch_desc(mB);
@@ -374,7 +378,9 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
         const int slen = slab_len(l);
         for (int s = 0; s * BK < slen; ++s, ++it) {
             const int stage = it % STAGES;
-            const bool got = mbar_wait_bounded(&full[stage], (it / STAGES) & 1);
+            const bool got = (g.stall_ns > 0 && it == 0)
+                                 ? mbar_wait_ns(never, 0, (uint64_t)g.stall_ns)
+                                 : mbar_wait_bounded(&full[stage], (it / STAGES) & 1);
             // every thread is past tile it-1 here, so its stage can be refilled
             if (!__syncthreads_and(got)) {
                 if (tid == 0) raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);

@@ -93,6 +93,9 @@ struct GemmArgs {
     // CTA computing one tile over one group and storing its packed slab
     // results; the launcher sets spg (slabs per group) and the final count
     int groups, spg;
+    // test of the bounded waits: > 0 makes every CTA's first wait for operand
+    // tiles wait on a barrier nothing completes, giving up after this many ns
+    long long stall_ns;
 };
 
 // 2-D TMA map over a row-major [rows][cols] array with leading dimension ld

@@ -86,3 +86,13 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.tdgemm_run(None, None, None, None, 1.0, 0.0, None) == 1
     assert lib.tdgemm_run_host(None, None, None, None, 1.0, 0.0, None) == 1
     assert lib.tdgemm_plan_destroy(None) == 0
+    assert lib.tdgemm_set_wait_test(None, 0) == 1
+
+
+def test_fma_probe_argument_checks(lib):
+    """The FMA-pipe probe rejects a bad dtype, a non-positive iteration count
+    and a NULL output before touching the device."""
+    fl = ctypes.c_double()
+    assert lib.tdgemm_fma_probe(5, 10, ctypes.byref(fl), None) == 1
+    assert lib.tdgemm_fma_probe(0, 0, ctypes.byref(fl), None) == 1
+    assert lib.tdgemm_fma_probe(0, 10, None, None) == 1

@@ -122,3 +122,69 @@ def test_mlp_training_50_steps(ag):
     got = train(True)
     assert got[-1] < 0.8 * got[0]
     assert abs(got[-1] - ref[-1]) < 0.05 * ref[0]
+
+
+@pytest.mark.parametrize("target", [20.0, 30.0])
+def test_config4_mlp_gradients_every_layer(ag, target):
+    """Config 4's MLP (128-1024-1024-10, tanh, batch 4096, synthetic teacher
+    labels, cross-entropy) at the student's initial weights: every layer's dW
+    from the companded-and-packed forward and adjoint products (fp32, sym,
+    W = 2, distortion target ``target``) against
+      (a) the exact fp64 gradient of the same loss, whole matrix (SNR), and
+      (b) central finite differences (h = 1e-6, fp64) of the smooth
+          (unquantized) loss at 16 sampled weights per layer, which first
+          agree with the fp64 autograd gradient (pinning the reference).
+    Straight-through: the gradient error is the companding noise of the
+    products on the path, so it is bounded by the target less the depth of
+    the chain (forward through up to three products, back through up to
+    three)."""
+    sizes = [128, 1024, 1024, 10]
+    teacher = [torch.from_numpy(w).cuda().double() for w in synth.mlp_teacher(sizes, 4)]
+    X32 = torch.from_numpy(synth.mlp_inputs(4096, 128, 5)).cuda()
+    X64 = X32.double()
+    with torch.no_grad():
+        h = X64
+        for k, w in enumerate(teacher):
+            h = h @ w
+            if k < 2:
+                h = torch.tanh(h)
+        labels = h.argmax(1)
+    init = [torch.from_numpy(w).cuda() for w in synth.mlp_teacher(sizes, 6)]
+    opts = dict(L=128, W=2, form="sym", target_snr_db=target)
+
+    def loss_of(ws, X, mm):
+        h = X
+        for k, w in enumerate(ws):
+            h = mm(h, w)
+            if k < 2:
+                h = torch.tanh(h)
+        return torch.nn.functional.cross_entropy(h, labels)
+
+    ws = [w.clone().requires_grad_() for w in init]
+    loss_of(ws, X32, lambda a, b: ag.tdg_matmul(a, b, **opts)).backward()
+    w64 = [w.double().clone().requires_grad_() for w in init]
+    loss_of(w64, X64, lambda a, b: a @ b).backward()
+
+    rng = np.random.default_rng(7)
+    h = 1e-6
+    for k in range(3):
+        g, g64 = ws[k].grad.double(), w64[k].grad
+        s = snr(g, g64)
+        assert s > target - 12.0, (k, s)
+        fds, got, ex = [], [], []
+        for _ in range(16):
+            i, j = int(rng.integers(sizes[k])), int(rng.integers(sizes[k + 1]))
+            vals = []
+            for d in (h, -h):
+                wd = [w.detach().double().clone() for w in init]
+                wd[k][i, j] += d
+                with torch.no_grad():
+                    vals.append(float(loss_of(wd, X64, lambda a, b: a @ b)))
+            fds.append((vals[0] - vals[1]) / (2 * h))
+            got.append(float(g[i, j]))
+            ex.append(float(g64[i, j]))
+        fds, got, ex = np.array(fds), np.array(got), np.array(ex)
+        ref_scale = math.sqrt(float(np.mean(fds * fds)))
+        assert np.sqrt(np.mean((ex - fds) ** 2)) < 1e-4 * ref_scale, k
+        rel = math.sqrt(float(np.mean((got - fds) ** 2))) / ref_scale
+        assert rel < 10 ** (-(target - 14.0) / 20), (k, rel)

@@ -116,3 +116,78 @@ def test_tc_precision_size_sampled(tdg, orc):
         rows, cols = (ti * 128, ti * 128 + 128), (tj * 128, tj * 128 + 128)
         ref = orc.tc_int_gemm(A, B, L=128, bits=0, rows=rows, cols=cols)
         assert same_bits(C[rows[0]:rows[1], cols[0]:cols[1]], ref.C), (ti, tj)
+
+
+def _fp8_bound(orc, A, B, ref, rows, cols, L=128):
+    """Elementwise bound on |C_gpu - C_oracle| for the E4M3 form over an output
+    window.  Both sides compute, per slab l, a sum of L exact products
+    a~ b~ (E4M3 products are exact in fp32), round it to fp32 (the oracle
+    once, the tensor core along its own accumulation order: at most L
+    roundings of 2^-24 relative to a partial sum no larger than
+    sum |a~ b~|), and then run the same fma chain over the slabs, whose nK
+    roundings differ by at most 2^-23 of its running magnitude.  So
+    |dC| <= (L + nK) 2^-23 sum_l (s_A s_B)_l sum_k |a~ b~|."""
+    r0, r1 = rows
+    c0, c1 = cols
+    K = A.shape[1]
+    nK = -(-K // L)
+    cA = np.repeat(ref.cA.astype(np.float32), L, 1)[:, :K]       # per (row block, k)
+    cB = np.repeat(ref.cB.astype(np.float32), L, 0)[:K]          # per (k, column block)
+    ib = np.arange(r0, r1) // L
+    jb = np.arange(c0, c1) // L
+    Aq = np.abs(orc.e4m3((A[r0:r1] * cA[ib]).astype(np.float64)))
+    Bq = np.abs(orc.e4m3((B[:, c0:c1] * cB[:, jb]).astype(np.float64)))
+    tot = np.zeros((r1 - r0, c1 - c0))
+    for l in range(nK):
+        k0, k1 = l * L, min(K, (l + 1) * L)
+        scale = np.outer(ref.sA[ib, l], ref.sB[l, jb])
+        tot += (Aq[:, k0:k1] @ Bq[k0:k1]) * scale
+    return (L + nK) * 2.0**-23 * tot
+
+
+def test_tc_fp8_multi_tile_persistent_full_c(tdg, orc):
+    """E4M3 and the integer form at 4000 x 400 x 3900: 256 output tile pairs
+    over at most 76 clusters, so every cluster walks several tiles and the
+    double-buffered accumulators' phases wrap many times (ragged M, N and a
+    16-wide last slab).  Integer form bit-exact over all of C; E4M3 within the
+    fp32 accumulation bound everywhere and whole-C SNR within 0.1 dB of the
+    oracle's."""
+    M, K, N = 4000, 400, 3900
+    A = synth.laplace((M, K), 61, np.float32)
+    B = synth.laplace((K, N), 62, np.float32)
+    ex = orc.exact_gemm(A, B)
+    ref_i = orc.tc_int_gemm(A, B, L=128, bits=8)
+    C, _ = run_tc(tdg, A, B, form="tc_int", bits=8)
+    assert same_bits(C, ref_i.C)
+    ref = orc.tc_fp8_gemm(A, B, L=128)
+    C, info = run_tc(tdg, A, B, form="tc_fp8")
+    assert info["carrier"] == 8
+    bound = _fp8_bound(orc, A, B, ref, (0, M), (0, N))
+    assert np.all(np.abs(C.astype(np.float64) - ref.C) <= bound + 1e-30)
+    assert abs(orc.snr_db(C, ex) - orc.snr_db(ref.C, ex)) < 0.1
+
+
+def test_tc_fp8_precision_size_sampled(tdg, orc):
+    """E4M3 at the precision-form workload, 8192^3 Laplacian(b = 1), L = 128:
+    13.5 tile pairs per cluster and 64 slabs per tile.  Three sampled 128 x 128
+    tiles over the full K (one in the last row and column of tiles) within the
+    fp32 accumulation bound, and their SNR within 0.1 dB of the oracle's."""
+    n = 8192
+    A = synth.laplace((n, n), 51, np.float32)
+    B = synth.laplace((n, n), 52, np.float32)
+    C, info = run_tc(tdg, A, B, form="tc_fp8")
+    tiles = synth.sample_tiles(64, 64, 2, seed=54) + [(63, 63)]
+    got, want, exact = [], [], []
+    for (ti, tj) in tiles:
+        rows, cols = (ti * 128, ti * 128 + 128), (tj * 128, tj * 128 + 128)
+        ref = orc.tc_fp8_gemm(A, B, L=128, rows=rows, cols=cols)
+        g = C[rows[0]:rows[1], cols[0]:cols[1]]
+        bound = _fp8_bound(orc, A, B, ref, rows, cols)
+        assert np.all(np.abs(g.astype(np.float64) - ref.C) <= bound + 1e-30), (ti, tj)
+        got.append(g)
+        want.append(ref.C)
+        exact.append(orc.exact_gemm(A, B, rows, cols))
+    ex = np.concatenate([e.ravel() for e in exact])
+    sg = orc.snr_db(np.concatenate([x.ravel() for x in got]), ex)
+    so = orc.snr_db(np.concatenate([x.ravel() for x in want]), ex)
+    assert abs(sg - so) < 0.1, (sg, so)
