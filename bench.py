@@ -696,6 +696,117 @@ def kernel_control_sweep(out_path=None):
     return recs
 
 
+def speedup_table(out_path=None) -> dict:
+    """F_W of Sec. 5.B on this GPU: the GEMM step (tdgemm_gemm alone) of the
+    inner-kernel-controlled symmetric product with every inner kernel
+    conventional (fraction 0) against every inner kernel packed at W
+    (fraction 1) -- the mixed launch that throughput control runs -- per
+    (dtype, W, L).  Writes it in the package's f_table.json format."""
+    import torch
+    from paper_1110_5765_gb300 import build as b
+    b.build()
+    import paper_1110_5765_gb300 as tdg
+    tables = {}
+    for dtype, n, Ls, reps in (("f32", 4096, (128, 256), 5), ("f64", 2048, (64, 128), 3)):
+        T = np.float32 if dtype == "f32" else np.float64
+        A = torch.from_numpy(synth.uniform((n, n), 31, T)).cuda()
+        B = torch.from_numpy(synth.uniform((n, n), 32, T)).cuda()
+        C = torch.empty_like(A)
+        for L in Ls:
+            for W in (2, 3, 4):
+                p = tdg.Plan(n, n, n, L=L, W=W, dtype=dtype, form="sym", bits=6,
+                             rep_noise=None, speedup=None)
+                t = {}
+                for frac in (0.0, 1.0):
+                    p.set_kernel_control("fraction", frac)
+                    p.run(A, B, C)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(reps):
+                        p.gemm(C)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    t[frac] = e0.elapsed_time(e1) / reps
+                p.close()
+                tables[f"{dtype}/sym/W{W}/L{L}"] = {"F": t[0.0] / t[1.0], "n": n,
+                                                    "t_conventional_ms": t[0.0],
+                                                    "t_packed_ms": t[1.0]}
+    out = {"about": ("F_W (Sec. 5.B): GEMM-step time of the inner-kernel-controlled symmetric "
+                     "product with all inner kernels conventional over all packed at W "
+                     "(tdgemm_gemm, CUDA events; fixed 6-bit companders; M = N = K = n)"),
+           "gpu": torch.cuda.get_device_name(), "tables": tables}
+    if out_path:
+        with open(out_path, "w") as f:
+            json.dump(out, f, indent=1)
+    print(json.dumps(out))
+    return out
+
+
+def fig6_study(out_path=None, ftab=None):
+    """Throughput-distortion curves at 4096^3 on the paper's generic input
+    family (uniform within 128 x 128 blocks, max_e per block drawn from
+    {4, 5, ..., 2048}, Sec. 7):
+      (a) distortion control (Fig. 6): the planner's SNR target 10..100 dB,
+          sGEMM (W <= 2) and dGEMM (W <= 4), the planner choosing W;
+      (b) throughput control (Sec. 6 (ii)): fp32 W = 2 plan at a 20 dB
+          target with a required acceleration F (mode 3) from 1.0 to F_W.
+    Each point: whole-path effective TFLOP/s = 2 M N K / t, its percentage of
+    the measured FMA-pipe peak of the dtype, the measured SNR against the
+    fp64 product, and (b) the number of inner kernels accelerated."""
+    import torch
+    from paper_1110_5765_gb300 import build as b
+    b.build()
+    import paper_1110_5765_gb300 as tdg
+    n = N_SIZE
+    pk = fma_peaks(tdg, torch)
+    flops = 2.0 * n ** 3
+    A32 = torch.from_numpy(synth.blockwise_range_uniform((n, n), 61, L_BLOCK, np.float32)).cuda()
+    B32 = torch.from_numpy(synth.blockwise_range_uniform((n, n), 62, L_BLOCK, np.float32)).cuda()
+    ref = torch.matmul(A32.double(), B32.double())
+    recs = {"peaks": pk, "distortion": [], "throughput": []}
+    for dtype, W in (("f32", 2), ("f64", 4)):
+        A = A32 if dtype == "f32" else A32.double()
+        B = B32 if dtype == "f32" else B32.double()
+        C = torch.empty_like(A)
+        reps = 3 if dtype == "f32" else 1
+        for target in range(10, 101, 10):
+            p = tdg.Plan(n, n, n, L=L_BLOCK, W=W, dtype=dtype, form="sym",
+                         target_snr_db=float(target))
+            t, tg = _time_split(p, A, B, C, torch, reps=reps)
+            info = p.info()
+            p.close()
+            tf = flops / t / 1e12
+            recs["distortion"].append({"dtype": dtype, "target_db": target, "W": info["W_used"],
+                                       "tflops": tf, "pct_peak": 100 * tf / pk[f"{dtype}_tflops"],
+                                       "snr_db": tdg.snr_db(C, ref),
+                                       "pred_snr_db": info["pred_snr_db"], "gemm_ms": tg * 1e3})
+    C = torch.empty_like(A32)
+    ftab = ftab if ftab is not None else "package"
+    p = tdg.Plan(n, n, n, L=L_BLOCK, W=2, dtype="f32", form="sym", target_snr_db=20.0,
+                 speedup=ftab)
+    fw = (ftab if isinstance(ftab, dict) else tdg.api.load_speedups()).get(
+        f"f32/sym/W2/L{L_BLOCK}", {}).get("F")
+    if fw:
+        for F in sorted({1.0, 1.1, 1.2, 1.3, 1.4, 1.5, round(fw, 3)}):
+            if F > fw:
+                continue
+            p.set_kernel_control("throughput", F)
+            t, tg = _time_split(p, A32, B32, C, torch, reps=3)
+            mask = p.kernel_mask()
+            tf = flops / t / 1e12
+            recs["throughput"].append({"F_target": F, "F_W": fw, "accelerated": int(mask.sum()),
+                                       "kernels": int(mask.size), "tflops": tf,
+                                       "pct_peak": 100 * tf / pk["f32_tflops"],
+                                       "snr_db": tdg.snr_db(C, ref), "gemm_ms": tg * 1e3})
+    p.close()
+    if out_path:
+        with open(out_path, "w") as f:
+            json.dump(recs, f, indent=1)
+    print(json.dumps(recs))
+    return recs
+
+
 def pca2d_study(out_path=None):
     """Sec. 8.A's 2DPCA face recognition with every GEMM through the library
     (Table 1's rows): synthetic faces (15 persons x 11 images of 288 x 288,
@@ -1141,7 +1252,21 @@ def main():
                     help="run the fixed-right-operand (packed B reuse) study")
     ap.add_argument("--fig7", default=None, metavar="OUT.json",
                     help="run the 4096^3 inner-kernel throughput-control sweep (Sec. 6)")
+    ap.add_argument("--fw", default=None, metavar="OUT.json",
+                    help="measure the F_W throughput-scaling table (Sec. 5.B)")
+    ap.add_argument("--fig6", default=None, metavar="OUT.json",
+                    help="throughput-distortion curves at 4096^3 (distortion and throughput "
+                         "control, Sec. 6-7)")
     args = ap.parse_args()
+    if args.fw:
+        speedup_table(args.fw)
+        return
+    if args.fig6:
+        fw = None
+        if not os.path.exists(os.path.join(ROOT, "paper_1110_5765_gb300", "f_table.json")):
+            fw = speedup_table()["tables"]
+        fig6_study(args.fig6, fw)
+        return
     if args.reuse:
         reuse_study(args.reuse)
         return

@@ -179,6 +179,15 @@ tdg_status tdgemm_set_manual(tdgemm_plan_t plan, int q, double c_a, double c_b);
  *   mode 2   fraction: accelerate the ceil(value * nM * nN) inner kernels
  *            of highest predicted S_ij / N_ij (ties to the lower row-major
  *            index); value in [0, 1]
+ *   mode 3   throughput (Sec. 6 (ii)): value = F >= 1, the required
+ *            acceleration of the product over the conventional one.  With
+ *            T = nM * nN inner kernels, each accelerated one taking 1 / F_W
+ *            of a conventional one's time (F_W of the packing the planner
+ *            chose, from tdgemm_set_speedup), accelerate the
+ *            k = ceil(T (1 - 1/F) / (1 - 1/F_W)) kernels of highest
+ *            predicted S_ij / N_ij (as mode 2): the fewest whose predicted
+ *            throughput T / ((T - k) + k / F_W) reaches F; none if F_W <= 1,
+ *            all if F >= F_W.  Needs F_W for every W the planner may choose.
  *
  * Valid for the SYM form with a planned (fixed-bit or target) plan without
  * TDG_KEEP_PACKED, at most 16384 inner kernels, and L a multiple of the GEMM
@@ -190,6 +199,15 @@ tdg_status tdgemm_set_manual(tdgemm_plan_t plan, int q, double c_a, double c_b);
  * on the first call that turns control on; they are freed with the plan.
  */
 tdg_status tdgemm_set_kernel_control(tdgemm_plan_t plan, int mode, double value);
+
+/*
+ * The measured throughput scaling F_W of Sec. 5.B: how many times faster an
+ * accelerated (packed, W) inner kernel runs than a conventional one on this
+ * GPU, measured offline for the plan's dtype, form and L (the package ships
+ * such a table, measured on GB300).  Used by throughput control (mode 3).
+ * W in 2..4, speedup > 0 and finite.
+ */
+tdg_status tdgemm_set_speedup(tdgemm_plan_t plan, int W, double speedup);
 
 /*
  * Copy the inner-kernel mask of the last tdgemm_quantize_pack to host memory:

@@ -26,7 +26,9 @@ What it computes, with the passage each step follows (Anastasia & Andreopoulos,
 * ``kernel_ratios``    Sec. 6: predicted signal-to-noise ratio of every inner
                        kernel (output block), eq. 21's terms summed over slabs
 * ``kernel_mask``      Sec. 6: the inner kernels accelerated under an SNR
-                       threshold or a fraction F of the best-predicted ones
+                       threshold, a fraction of the best-predicted ones, or a
+                       throughput target through the measured F_W (Sec. 5.B)
+                       (``kernels_for_throughput``)
 * ``pair_companders``, ``tdgemm_pair_exact``
                        eq. 26 per subblock product (Prop. 4): each (i, l, j)
                        pair's Gamma_A, Gamma_B split within the call's R_max
@@ -469,18 +471,41 @@ def kernel_ratios(stA: BlockStats, stB: BlockStats, L: int, gA: int, gB: int, s:
     return out
 
 
-def kernel_mask(ratios: np.ndarray, mode: str, value: float) -> np.ndarray:
+def kernels_for_throughput(T: int, F: float, F_W: float) -> int:
+    """Sec. 6 (ii) with the inner kernel as the unit of control: the fewest of
+    the T inner kernels to accelerate so that the predicted acceleration of
+    the whole product over the conventional one reaches F.  An accelerated
+    kernel takes 1 / F_W of a conventional kernel's time (F_W: the measured
+    throughput scaling of packing W, Sec. 5.B), so k accelerated kernels give
+    T / ((T - k) + k / F_W) >= F  <=>  k >= T (1 - 1/F) / (1 - 1/F_W).
+    F <= 1 or F_W <= 1 (packing no faster): none; F >= F_W: all (the most
+    that packing W can give)."""
+    if not (F > 1.0) or not (F_W > 1.0):
+        return 0
+    if F >= F_W:
+        return T
+    x = (float(T) * (1.0 - 1.0 / F)) / (1.0 - 1.0 / F_W)
+    return max(0, min(T, int(math.ceil(x))))
+
+
+def kernel_mask(ratios: np.ndarray, mode: str, value: float,
+                F_W: float | None = None) -> np.ndarray:
     """Which inner kernels run packed (Sec. 6, one W for the accelerated ones):
-    'snr'      -- those whose predicted SNR meets S_kernel = value dB
-                  (ratio >= 10^(value/10));
-    'fraction' -- throughput control: the ceil(value * T) kernels with the
-                  highest predicted SNR (ties to the lower row-major index)."""
+    'snr'        -- those whose predicted SNR meets S_kernel = value dB
+                    (ratio >= 10^(value/10));
+    'fraction'   -- the ceil(value * T) kernels with the highest predicted SNR
+                    (ties to the lower row-major index);
+    'throughput' -- throughput control: as 'fraction', with the count from
+                    ``kernels_for_throughput(T, value, F_W)``."""
     T = ratios.size
     flat = ratios.ravel()
     if mode == "snr":
         thr = math.pow(10.0, value / 10.0)
         return (flat >= thr).reshape(ratios.shape)
-    k = int(math.ceil(value * T))
+    if mode == "throughput":
+        k = kernels_for_throughput(T, value, F_W)
+    else:
+        k = int(math.ceil(value * T))
     order = sorted(range(T), key=lambda t: (-flat[t], t))
     m = np.zeros(T, dtype=bool)
     for t in order[:k]:
@@ -609,8 +634,9 @@ def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: st
     (given integer companders).  ``noise_rms`` (the default) selects the
     RMS-scaled representation noise of ``model_noise``; False takes s as
     calibrated on uniform integers, unscaled.  ``kernel_control = (mode,
-    value)`` ('snr' or 'fraction', Sec. 6) computes the inner kernels that
-    ``kernel_mask`` leaves out with the conventional product instead.  ``rows``/``cols`` restrict the computed
+    value)`` ('snr' or 'fraction', Sec. 6), or ``('throughput', F, {W: F_W})``,
+    computes the inner kernels that ``kernel_mask`` leaves out with the
+    conventional product instead.  ``rows``/``cols`` restrict the computed
     outputs to a window (for asym, row windows must align to L)."""
     T = NP_T[dtype]
     A = np.ascontiguousarray(A, dtype=T)
@@ -685,7 +711,11 @@ def tdgemm(A: np.ndarray, B: np.ndarray, *, L: int, W: int, dtype: str, form: st
     if kernel_control is not None and form == "sym":
         s_rep = pl.extra.get("s_rep", 0.0)
         ratios = kernel_ratios(stA, stB, L, pl.gA, pl.gB, s_rep, noise_rms)
-        mask = kernel_mask(ratios, *kernel_control)
+        if kernel_control[0] == "throughput":
+            # ("throughput", F, {W: F_W}): the speed-up of the packing the planner chose
+            mask = kernel_mask(ratios, "throughput", kernel_control[1], kernel_control[2][pl.W])
+        else:
+            mask = kernel_mask(ratios, *kernel_control)
         pl.extra["kernel_mask"] = mask
         plain = gemm_plain(A, B, dtype, (r0, r1), (c0, c1))
         for m in range(r0, r1):

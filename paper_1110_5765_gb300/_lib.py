@@ -29,6 +29,7 @@ EXPORTS = ["tdgemm_plan", "tdgemm_set_rep_noise", "tdgemm_set_manual",
            "tdgemm_quantize_pack_a",
            "tdgemm_gemm", "tdgemm_run", "tdgemm_run_host", "tdgemm_unpack", "tdgemm_plan_info",
            "tdgemm_plan_destroy", "tdgemm_snr", "tdgemm_run_static", "tdgemm_set_wait_test",
+           "tdgemm_set_speedup",
            "tdgemm_fma_probe", "tdgemm_last_error", "tdgemm_version"]
 
 
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.tdgemm_run_static.argtypes = [ctypes.c_char, ctypes.c_char, i64, i64, i64, i64, i64, i64,
                                     i32, i32, i32, i32, i32, vp, vp, vp, dbl, dbl, vp]
     L.tdgemm_set_wait_test.argtypes = [vp, i64]
+    L.tdgemm_set_speedup.argtypes = [vp, i32, dbl]
     L.tdgemm_fma_probe.argtypes = [i32, i64, ctypes.POINTER(dbl), vp]
     L.tdgemm_last_error.restype = ctypes.c_char_p
     L.tdgemm_version.restype = ctypes.c_char_p

@@ -23,6 +23,7 @@ from ._lib import (DTYPES, FORMS, TDG_ALLOW_FALLBACK, TDG_KEEP_PACKED, TDG_NOISE
 _TORCH_DT = {"f32": torch.float32, "f64": torch.float64}
 _DT_OF = {torch.float32: "f32", torch.float64: "f64"}
 S_TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "s_table.json")
+F_TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "f_table.json")
 MAX_LEVELS = 192
 
 _table_cache: dict | None = None
@@ -41,6 +42,15 @@ def load_rep_noise(path: str = S_TABLE_PATH) -> dict:
     if path == S_TABLE_PATH:
         _table_cache = tabs
     return tabs
+
+
+def load_speedups(path: str = F_TABLE_PATH) -> dict:
+    """The package's measured throughput-scaling table F_W (Sec. 5.B), keyed
+    ``"{dtype}/{form}/W{W}/L{L}" -> {"F": ...}``; empty if absent."""
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return json.load(f)["tables"]
 
 
 def rep_noise_table(dtype: str, form: str, W: int, L: int, tables: dict | None = None):
@@ -93,7 +103,8 @@ class Plan:
                  transA: str = "N", transB: str = "N", lda: int | None = None,
                  ldb: int | None = None, ldc: int | None = None, allow_fallback: bool = True,
                  keep_packed: bool = False, rep_noise: str | dict | None = "package",
-                 noise_rms: bool = True, pair_exact: bool = False):
+                 noise_rms: bool = True, pair_exact: bool = False,
+                 speedup: str | dict | None = "package"):
         self._L = _lib.load()
         self.M, self.N, self.K = int(M), int(N), int(K)
         self.L, self.W, self.dtype, self.form = int(L), int(W), dtype, form
@@ -115,6 +126,12 @@ class Plan:
                 arr = rep_noise_table(dtype, form, w, self.L, tables)
                 if arr is not None:
                     self.set_rep_noise(w, arr, 0)
+        if form == "sym" and speedup is not None:
+            ftab = load_speedups() if speedup == "package" else speedup
+            for w in range(2, self.W + 1):
+                d = ftab.get(f"{dtype}/{form}/W{w}/L{self.L}")
+                if d:
+                    self.set_speedup(w, float(d["F"]))
 
     # -- configuration
     def set_rep_noise(self, W: int, s, t0: int = 0):
@@ -126,13 +143,20 @@ class Plan:
     def set_manual(self, q: int, c_a: float = 1.0, c_b: float = 1.0):
         check(self._L.tdgemm_set_manual(self._h, int(q), float(c_a), float(c_b)))
 
-    _KCTRL = {None: 0, "off": 0, "snr": 1, "fraction": 2}
+    def set_speedup(self, W: int, speedup: float):
+        """F_W of Sec. 5.B for packing W (throughput control)."""
+        check(self._L.tdgemm_set_speedup(self._h, int(W), float(speedup)))
+
+    _KCTRL = {None: 0, "off": 0, "snr": 1, "fraction": 2, "throughput": 3}
 
     def set_kernel_control(self, mode: str | None, value: float = 0.0):
         """Sec. 6 control over inner kernels: mode 'snr' accelerates the L x L
         output blocks whose predicted SNR (dB) reaches ``value``, 'fraction'
-        the ``ceil(value * nM * nN)`` blocks of highest predicted SNR; the
-        others are computed with the conventional product.  None turns it off."""
+        the ``ceil(value * nM * nN)`` blocks of highest predicted SNR,
+        'throughput' the fewest of highest predicted SNR whose predicted
+        acceleration over the conventional product reaches ``value`` (through
+        the measured F_W); the others are computed with the conventional
+        product.  None turns it off."""
         check(self._L.tdgemm_set_kernel_control(self._h, self._KCTRL[mode], float(value)))
 
     def set_wait_test(self, limit_ns: int):

@@ -87,9 +87,12 @@ struct tdgemm_plan_s {
     int kctrl_mode = 0;
     double kctrl_value = 0.0, kctrl_thr = 0.0;
     long long kctrl_k = 0;
+    Speedups speedup{};                       // F_W by W (Sec. 5.B), 0 = not given
     void *kA = nullptr, *kB = nullptr;        // plain k-major copies for unaccelerated kernels
     double *kratio = nullptr;
     unsigned char *kmask = nullptr;
+    int *korder = nullptr;                    // launch order of the mixed GEMM's tiles
+    long long ktiles_m = 0, ktiles_n = 0;
     // state
     const void *A_user = nullptr, *B_user = nullptr;
     bool packed = false, gemm_done = false, b_packed = false;
@@ -343,12 +346,21 @@ extern "C" tdg_status tdgemm_set_kernel_control(tdgemm_plan_t p, int mode, doubl
     if (mode == 0) { p->kctrl_mode = 0; p->packed = p->b_packed = false; return TDG_OK; }
     if (p->form != TDG_SYM) return fail(TDG_EINVAL, "inner-kernel control needs the SYM form");
     if (p->mode == MODE_MANUAL) return fail(TDG_EINVAL, "inner-kernel control needs a planned (not manual) plan");
-    if (mode != 1 && mode != 2) return fail(TDG_EINVAL, "mode must be 0, 1 (SNR) or 2 (fraction)");
+    if (mode < 1 || mode > 3)
+        return fail(TDG_EINVAL, "mode must be 0, 1 (SNR), 2 (fraction) or 3 (throughput)");
     if (p->flags & (TDG_KEEP_PACKED | TDG_PAIR_EXACT))
         return fail(TDG_EINVAL,
                     "inner-kernel control works without TDG_KEEP_PACKED and TDG_PAIR_EXACT");
     if (!isfinite(value)) return fail(TDG_EINVAL, "value must be finite");
     if (mode == 2 && (value < 0.0 || value > 1.0)) return fail(TDG_EINVAL, "fraction must be in [0, 1]");
+    if (mode == 3) {
+        if (value < 1.0) return fail(TDG_EINVAL, "throughput target must be >= 1 (x the conventional product)");
+        // the device planner may choose any packing from W down to 2
+        const int wlo = p->mode == MODE_TARGET ? 2 : p->W;
+        for (int w = wlo; w <= p->W; ++w)
+            if (!(p->speedup.fw[w] > 0.0))
+                return fail(TDG_EINVAL, "throughput control needs F_W for W = %d (tdgemm_set_speedup)", w);
+    }
     {
         // the mixed launch runs both kinds of tile with one box shape
         int sa, sb, sk, pa, pb, pk;
@@ -364,9 +376,14 @@ extern "C" tdg_status tdgemm_set_kernel_control(tdgemm_plan_t p, int mode, doubl
     const long long T = (long long)p->nM * p->nN;
     if (T > 16384) return fail(TDG_EINVAL, "inner-kernel control supports up to 16384 inner kernels");
     if (!p->kratio) {
+        int bm, bn, bk;
+        packed_gemm_boxes(p->dtype, G_SYM, 2, &bm, &bn, &bk);
+        p->ktiles_m = (p->M + bm - 1) / bm;
+        p->ktiles_n = (p->N + bn - 1) / bn;
         CU_TRY(cudaMalloc(&p->kratio, (size_t)T * 8));
         CU_TRY(cudaMalloc(&p->kmask, (size_t)T));
         CU_TRY(cudaMemset(p->kmask, 0, (size_t)T));
+        CU_TRY(cudaMalloc(&p->korder, (size_t)(p->ktiles_m * p->ktiles_n) * sizeof(int)));
     }
     if (!p->kA) {
         OpShape s = op_shape(p, 0);
@@ -378,6 +395,15 @@ extern "C" tdg_status tdgemm_set_kernel_control(tdgemm_plan_t p, int mode, doubl
     p->kctrl_thr = mode == 1 ? pow(10.0, value / 10.0) : 0.0;
     p->kctrl_k = mode == 2 ? (long long)ceil(value * (double)T) : 0;
     p->packed = p->b_packed = false;   // the packed operands no longer match: pack again
+    return TDG_OK;
+}
+
+extern "C" tdg_status tdgemm_set_speedup(tdgemm_plan_t p, int W, double speedup) {
+    if (!p) return fail(TDG_EINVAL, "plan is NULL");
+    if (W < 2 || W > kMaxW) return fail(TDG_EINVAL, "W must be in 2..4");
+    if (!(speedup > 0.0) || !isfinite(speedup)) return fail(TDG_EINVAL, "F_W must be positive and finite");
+    p->speedup.fw[W] = speedup;
+    if (p->kctrl_mode == 3) p->packed = p->b_packed = false;   // the mask changes: pack again
     return TDG_OK;
 }
 
@@ -467,7 +493,14 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
                                    (T *)p->cBpx, (T *)p->pairpx, st));
     if (p->kctrl_mode) {
         CU_TRY(launch_kernel_control(pp, p->mA, p->eA, p->mB, p->eB, p->dplan, p->kctrl_mode,
-                                     p->kctrl_thr, p->kctrl_k, p->kratio, p->kmask, st));
+                                     p->kctrl_thr, p->kctrl_k, p->kctrl_value, p->speedup,
+                                     p->kratio, p->kmask, st));
+        {
+            int bm, bn, bk;
+            packed_gemm_boxes(p->dtype, G_SYM, 2, &bm, &bn, &bk);
+            CU_TRY(launch_tile_order(p->kmask, p->nN, p->L, bm, bn, p->ktiles_m, p->ktiles_n,
+                                     p->korder, st));
+        }
         OpShape s0 = op_shape(p, 0);
         const bool directA = !nA && (p->lda * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)A & 15) == 0;
         const bool directB = nB && (p->ldb * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)B & 15) == 0;
@@ -604,6 +637,7 @@ static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cu
             // conventional product from the plain operands, same launch
             plain_ops(p->kA, p->kB, ops.pa, ops.pb);
             g.kmask = p->kmask;
+            g.tile_order = p->korder;
         }
         cudaError_t e;
         if (!plain && (p->flags & TDG_PAIR_EXACT)) {
@@ -779,6 +813,7 @@ extern "C" tdg_status tdgemm_plan_destroy(tdgemm_plan_t p) {
     if (p->kB) cudaFree(p->kB);
     if (p->kratio) cudaFree(p->kratio);
     if (p->kmask) cudaFree(p->kmask);
+    if (p->korder) cudaFree(p->korder);
     delete p;
     return TDG_OK;
 }

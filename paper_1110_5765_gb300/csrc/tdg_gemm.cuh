@@ -233,7 +233,10 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
     // (KEEP instantiation, groups > 1) CTA b takes tile b % ntiles and the
     // slabs of group b / ntiles
     const bool split = KEEP && g.groups > 1;
-    const long long tix = split ? (long long)blockIdx.x % g.ntiles : (long long)blockIdx.x;
+    long long tix = split ? (long long)blockIdx.x % g.ntiles : (long long)blockIdx.x;
+    if constexpr (MIX) {
+        if (g.tile_order) tix = g.tile_order[blockIdx.x];
+    }
     const long long tmi = tix / g.ntn;
     const long long x0 = tmi * BM;                      // first A-operand column (m or packed row)
     const long long n0 = (tix - tmi * g.ntn) * BN;

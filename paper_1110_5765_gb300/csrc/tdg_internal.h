@@ -45,12 +45,28 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
                            DevPlan *plan, double *agg, T *cA, double *sA, T *cB, double *sB,
                            T *pair, cudaStream_t st);
 
+// Launch order of the tiles of a mixed (Sec. 6) launch: the tiles of
+// unaccelerated inner kernels first, then the accelerated ones, each group in
+// row-major order; tile (tm, tn) of the tiles_m x ntn grid of bm x bn tiles
+// lies in inner kernel (tm bm / L, tn bn / L).
+cudaError_t launch_tile_order(const unsigned char *mask, int nN, int L, int bm, int bn,
+                              long long tiles_m, long long ntn, int *order, cudaStream_t st);
+
+// Measured throughput scaling F_W of an accelerated inner kernel over a
+// conventional one (Sec. 5.B), by packing W (index 2..4; <= 0: not measured).
+struct Speedups {
+    double fw[kMaxW + 1];
+};
+
 // Sec. 6 inner-kernel control: per-kernel predicted S/N and the mask of
-// kernels that run packed (mode 1: S/N >= thr; mode 2: the k best).
+// kernels that run packed (mode 1: S/N >= thr; mode 2: the k best; mode 3:
+// the fewest best whose predicted acceleration reaches F through the F_W of
+// the packing the device planner chose).
 cudaError_t launch_kernel_control(const PlanParams &pp, const double *mA, const double *vA,
                                   const double *mB, const double *vB, const DevPlan *plan,
-                                  int mode, double thr, long long k, double *ratio,
-                                  unsigned char *mask, cudaStream_t st);
+                                  int mode, double thr, long long k, double F,
+                                  const Speedups &fw, double *ratio, unsigned char *mask,
+                                  cudaStream_t st);
 
 // Pack kernels run only when the device plan's W equals expectW (expectW = 0:
 // always); W is the
@@ -86,6 +102,10 @@ struct GemmArgs {
     // CTA tile whose kernel's mask is 0 computes the conventional product from
     // the plain operands in the same launch.
     const unsigned char *kmask;
+    // nullable (with kmask): tile to run for each CTA index, the
+    // conventional-product tiles first (they take about W times longer, so
+    // starting them first keeps the last wave short)
+    const int *tile_order;
     const T *cApx, *cBpx;   // pair-exact companders [(i nK + l) nN + j] (else unused)
     int ntn;                // set by the launcher: tiles per row of the 1-D tile grid
     long long ntiles;       // set by the launcher: tiles in the grid

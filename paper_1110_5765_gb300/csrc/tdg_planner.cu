@@ -410,20 +410,36 @@ __global__ void kernel_ratio_kernel(PlanParams pp, const double *__restrict__ mA
     if (lane == 0) ratio[t] = N > 0.0 ? __ddiv_rn(S, N) : INFINITY;
 }
 
+// Sec. 6 (ii): the fewest of T inner kernels whose acceleration makes the
+// product's predicted throughput T / ((T - k) + k / F_W) reach F, i.e.
+// k = ceil(T (1 - 1/F) / (1 - 1/F_W)); none if F <= 1 or F_W <= 1, all if
+// F >= F_W.  Every operation rounded as written (the oracle's order).
+__device__ inline long long kernels_for_throughput(long long T, double F, double fw) {
+    if (!(F > 1.0) || !(fw > 1.0)) return 0;
+    if (F >= fw) return T;
+    const double x = __ddiv_rn(__dmul_rn((double)T, __dsub_rn(1.0, __ddiv_rn(1.0, F))),
+                               __dsub_rn(1.0, __ddiv_rn(1.0, fw)));
+    const long long k = (long long)ceil(x);
+    return k < 0 ? 0 : (k > T ? T : k);
+}
+
 // mode 1: ratio >= thr;  mode 2: rank (descending ratio, ties to the lower
-// index) below k, counted against the ratios staged through shared memory.
-// Ratios are non-negative (or +inf), so their bit patterns order like the
-// values and the O(T^2) rank count runs on the integer pipe.  A plan that fell
-// back to W = 1 accelerates nothing.
+// index) below k, counted against the ratios staged through shared memory;
+// mode 3: as mode 2 with k from the throughput target.  Ratios are
+// non-negative (or +inf), so their bit patterns order like the values and the
+// O(T^2) rank count runs on the integer pipe.  A plan that fell back to W = 1
+// accelerates nothing.
 constexpr int kMaskThreads = 128, kMaskChunk = 2048;
 __global__ void __launch_bounds__(kMaskThreads)
-    kernel_mask_kernel(long long T, int mode, double thr, long long k,
+    kernel_mask_kernel(long long T, int mode, double thr, long long k, double F, Speedups fw,
                        const DevPlan *__restrict__ plan, const double *__restrict__ ratio,
                        unsigned char *mask) {
     pdl_entry();
     __shared__ unsigned long long chunk[kMaskChunk];
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool fell_back = plan->W < 2;      // uniform
+    const int W = plan->W;
+    const bool fell_back = W < 2;            // uniform
+    if (mode == 3 && !fell_back) k = kernels_for_throughput(T, F, fw.fw[min(W, kMaxW)]);
     if (fell_back || mode == 1) {
         if (t < T) mask[t] = fell_back ? 0 : (ratio[t] >= thr ? 1 : 0);
         return;
@@ -446,19 +462,61 @@ __global__ void __launch_bounds__(kMaskThreads)
     if (t < T) mask[t] = rank < k ? 1 : 0;
 }
 
+// One CTA: each thread counts the conventional tiles in its contiguous chunk
+// of the row-major tile list, a block-wide exclusive scan gives every chunk
+// its first position in both groups, and the chunk is written out.
+constexpr int kOrderThreads = 1024;
+__global__ void __launch_bounds__(kOrderThreads)
+    tile_order_kernel(const unsigned char *__restrict__ mask, int nN, int L, int bm, int bn,
+                      long long tiles_m, long long ntn, int *__restrict__ order) {
+    pdl_entry();
+    __shared__ long long scan[kOrderThreads];
+    const long long n = tiles_m * ntn;
+    const long long chunk = (n + kOrderThreads - 1) / kOrderThreads;
+    const long long t0 = min(n, (long long)threadIdx.x * chunk), t1 = min(n, t0 + chunk);
+    auto conventional = [&](long long t) {
+        const long long tm = t / ntn, tn = t - tm * ntn;
+        return mask[(tm * bm / L) * nN + (tn * bn / L)] == 0;
+    };
+    long long mine = 0;
+    for (long long t = t0; t < t1; ++t) mine += conventional(t) ? 1 : 0;
+    scan[threadIdx.x] = mine;
+    __syncthreads();
+    for (int off = 1; off < kOrderThreads; off <<= 1) {     // inclusive scan
+        const long long v = threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
+        __syncthreads();
+        scan[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const long long total_conv = scan[kOrderThreads - 1];
+    long long pc = scan[threadIdx.x] - mine;                 // conventional tiles before t0
+    long long pp = total_conv + (t0 - pc);                   // accelerated tiles before t0, offset
+    for (long long t = t0; t < t1; ++t) {
+        if (conventional(t)) order[pc++] = (int)t;
+        else order[pp++] = (int)t;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_tile_order(const unsigned char *mask, int nN, int L, int bm, int bn,
+                              long long tiles_m, long long ntn, int *order, cudaStream_t st) {
+    return launch_pdl(tile_order_kernel, dim3(1), dim3(kOrderThreads), 0, st, mask, nN, L, bm,
+                      bn, tiles_m, ntn, order);
+}
 
 cudaError_t launch_kernel_control(const PlanParams &pp, const double *mA, const double *vA,
                                   const double *mB, const double *vB, const DevPlan *plan,
-                                  int mode, double thr, long long k, double *ratio,
-                                  unsigned char *mask, cudaStream_t st) {
+                                  int mode, double thr, long long k, double F,
+                                  const Speedups &fw, double *ratio, unsigned char *mask,
+                                  cudaStream_t st) {
     const long long T = (long long)pp.nM * pp.nN;
     cudaError_t e = launch_pdl(kernel_ratio_kernel, dim3((unsigned)((T * 32 + 255) / 256)),
                                dim3(256), 0, st, pp, mA, vA, mB, vB, plan, ratio);
     if (e != cudaSuccess) return e;
     return launch_pdl(kernel_mask_kernel,
                       dim3((unsigned)((T + kMaskThreads - 1) / kMaskThreads)), dim3(kMaskThreads),
-                      0, st, T, mode, thr, k, plan, (const double *)ratio, mask);
+                      0, st, T, mode, thr, k, F, fw, plan, (const double *)ratio, mask);
 }
 
 template <typename T>

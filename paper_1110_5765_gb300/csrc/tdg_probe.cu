@@ -3,12 +3,15 @@
 // their roofline fraction is taken against this rate (the measured bf16
 // peak of the tensor pipe does not apply to them).
 //
-// Each thread runs kChains independent accumulation chains x <- fma(x, a, b)
-// (a = 1 - 2^-12, b = 2^-12: every chain converges to 1, no overflow or
-// subnormals), enough to cover the pipe's latency; the launch holds a full
-// occupancy of 256-thread CTAs on every SM.  Nothing is read or written in
-// memory: the chains' sum is compared with a NaN argument and stored only if
-// equal, which never happens, but keeps the compiler from removing the work.
+// Each thread runs kChains independent accumulation chains
+// acc <- fma(a_c, b, acc), the accumulator as the addend as in the GEMM's main
+// loop (with the accumulator as a multiplicand GB300's FP64 pipe measured
+// about 15 % slower), enough to cover the pipe's latency; the launch holds a
+// full occupancy of 256-thread CTAs on every SM.  a_c b is 2^-24 or so, so
+// the sums stay near 1 (no overflow, no subnormals).  Nothing is read or
+// written in memory: the chains' sum is compared with a NaN argument and
+// stored only if equal, which never happens, but keeps the compiler from
+// removing the work.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,26 +27,25 @@ constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads) fma_probe_f32x2(long long iters, float never,
                                                             float *sink) {
-    uint64_t x[kChains];
-    uint64_t a2, b2;
-    const float a = 1.0f - 1.0f / 4096.0f, b = 1.0f / 4096.0f;
-    asm("mov.b64 %0, {%1, %1};" : "=l"(a2) : "f"(a));
+    uint64_t acc[kChains], a2[kChains], b2;
+    const float b = 1.0f / 4096.0f;
     asm("mov.b64 %0, {%1, %1};" : "=l"(b2) : "f"(b));
 #pragma unroll
     for (int c = 0; c < kChains; ++c) {
-        const float v = (float)(threadIdx.x + c) * 1e-3f;
-        asm("mov.b64 %0, {%1, %2};" : "=l"(x[c]) : "f"(v), "f"(-v));
+        const float a = (1.0f + (float)c / 64.0f) / 4096.0f;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(a2[c]) : "f"(a), "f"(-a));
+        asm("mov.b64 %0, {%1, %1};" : "=l"(acc[c]) : "f"(1.0f + (float)threadIdx.x * 1e-3f));
     }
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int c = 0; c < kChains; ++c)
-            asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[c]) : "l"(a2), "l"(b2));
+            asm volatile("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[c]) : "l"(a2[c]), "l"(b2));
     }
     float s = 0.f;
 #pragma unroll
     for (int c = 0; c < kChains; ++c) {
         float lo, hi;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x[c]));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[c]));
         s += lo + hi;
     }
     if (s == never) sink[threadIdx.x] = s;
@@ -51,18 +53,21 @@ __global__ void __launch_bounds__(kThreads) fma_probe_f32x2(long long iters, flo
 
 __global__ void __launch_bounds__(kThreads) fma_probe_f64(long long iters, double never,
                                                           double *sink) {
-    double x[kChains];
-    const double a = 1.0 - 1.0 / 4096.0, b = 1.0 / 4096.0;
+    double acc[kChains], a[kChains];
+    const double b = 1.0 / 4096.0;
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) x[c] = (double)(threadIdx.x + c) * 1e-3;
+    for (int c = 0; c < kChains; ++c) {
+        a[c] = (1.0 + (double)c / 64.0) / 4096.0;
+        acc[c] = 1.0 + (double)threadIdx.x * 1e-3;
+    }
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int c = 0; c < kChains; ++c)
-            asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(x[c]) : "d"(a), "d"(b));
+            asm volatile("fma.rn.f64 %0, %1, %2, %0;" : "+d"(acc[c]) : "d"(a[c]), "d"(b));
     }
     double s = 0.0;
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) s += x[c];
+    for (int c = 0; c < kChains; ++c) s += acc[c];
     if (s == never) sink[threadIdx.x] = s;
 }
 

@@ -45,11 +45,11 @@ def inputs(shape_mkn, L, dtype, seed):
 
 
 def run_ctrl(tdg, A, B, *, L, W, dtype, bits=0, target=math.nan, ctrl, rms=False,
-             alpha=1.0, beta=0.0, Cin=None, dense=None):
+             alpha=1.0, beta=0.0, Cin=None, dense=None, speedup=None):
     M, K = A.shape
     N = B.shape[1]
     p = tdg.Plan(M, N, K, L=L, W=W, dtype=dtype, form="sym", bits=bits, target_snr_db=target,
-                 rep_noise=None, noise_rms=rms)
+                 rep_noise=None, noise_rms=rms, speedup=speedup)
     if dense is not None:
         for w, arr in dense.items():
             p.set_rep_noise(w, arr, 0)
@@ -211,3 +211,72 @@ def test_control_off_again_and_argument_checks(tdg, orc):
             q.set_kernel_control("fraction", 0.5)
         assert e.value.status == 1
         q.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[3])
+@pytest.mark.parametrize("F", [1.0, 1.25, 1.5, 3.0])
+def test_throughput_mode_matches_oracle(tdg, orc, case, F):
+    """Sec. 6 (ii): a throughput target F (x the conventional product) through
+    the measured F_W (here 1.7): the device computes the kernel count from
+    the packing the planner chose; mask and C bit-identical to the oracle."""
+    shape, L, W, dtype, bits = case
+    A, B = inputs(shape, L, dtype, 750 + bits)
+    ref = orc.tdgemm(A, B, L=L, W=W, dtype=dtype, form="sym", bits=bits,
+                     kernel_control=("throughput", F, {W: 1.7}))
+    C, mask, _ = run_ctrl(tdg, A, B, L=L, W=W, dtype=dtype, bits=bits, ctrl=("throughput", F),
+                          speedup={f"{dtype}/sym/W{W}/L{L}": {"F": 1.7}})
+    T = mask.size
+    assert int(mask.sum()) == orc.kernels_for_throughput(T, F, 1.7)
+    assert np.array_equal(mask.astype(bool), ref.plan.extra["kernel_mask"])
+    assert same_bits(C, ref.C)
+
+
+def test_throughput_mode_uses_the_planned_packing(tdg, orc):
+    """Distortion-target plan (W chosen on the device among 3 and 2) with
+    different F_W per packing: the count follows the F_W of the chosen W."""
+    dtype, L, W = "f32", 128, 3
+    A, B = inputs((384, 512, 400), L, dtype, 911)
+    dense, tabs = {}, {}
+    for w in (2, 3):
+        d, arr = {}, np.full(192, -1.0)
+        for t in range(0, orc.T_MAX[dtype] + 1):
+            R = orc.r_level(t)
+            s = 1e-3 * R * (w - 1) if R >= L else 0.0
+            d[str(t)] = {"s": s}
+            arr[t] = s
+        tabs[orc.STable.key(dtype, "sym", w, L)] = d
+        dense[w] = arr
+    st = orc.STable(tabs)
+    fw = {2: 1.55, 3: 2.2}
+    seen = set()
+    for target, F in ((15.0, 1.4), (25.0, 1.3)):       # the planner packs W = 3, then W = 2
+        ref = orc.tdgemm(A, B, L=L, W=W, dtype=dtype, form="sym", target_db=target, s_table=st,
+                         kernel_control=("throughput", F, fw))
+        seen.add(ref.plan.W)
+        C, mask, info = run_ctrl(tdg, A, B, L=L, W=W, dtype=dtype, target=target, rms=True,
+                                 ctrl=("throughput", F), dense=dense,
+                                 speedup={f"{dtype}/sym/W{w}/L{L}": {"F": v} for w, v in fw.items()})
+        assert info["W_used"] == ref.plan.W >= 2
+        assert int(mask.sum()) == orc.kernels_for_throughput(mask.size, F, fw[ref.plan.W])
+        assert np.array_equal(mask.astype(bool), ref.plan.extra["kernel_mask"])
+        assert same_bits(C, ref.C)
+    assert seen == {2, 3}
+
+
+def test_throughput_mode_argument_checks(tdg):
+    from paper_1110_5765_gb300._lib import TDGemmError
+    p = tdg.Plan(256, 256, 256, L=128, W=2, dtype="f32", form="sym", bits=6, rep_noise=None,
+                 speedup=None)
+    with pytest.raises(TDGemmError) as e:
+        p.set_kernel_control("throughput", 1.3)     # no F_W given
+    assert e.value.status == 1
+    p.set_speedup(2, 1.6)
+    with pytest.raises(TDGemmError) as e:
+        p.set_kernel_control("throughput", 0.9)     # below the conventional product
+    assert e.value.status == 1
+    p.set_kernel_control("throughput", 1.3)
+    with pytest.raises(TDGemmError):
+        p.set_speedup(5, 1.5)
+    with pytest.raises(TDGemmError):
+        p.set_speedup(2, -1.0)
+    p.close()

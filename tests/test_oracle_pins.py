@@ -534,6 +534,55 @@ def test_kernel_snr_prediction_against_measurement(orc, gen):
             assert lo < d < hi, (i, j, d)
 
 
+def test_throughput_kernel_count_is_the_fewest_meeting_the_target(orc):
+    """Sec. 6 (ii) through the measured F_W of Sec. 5.B: the count the closed
+    form gives is the smallest k with T / ((T - k) + k / F_W) >= F, found by
+    exhaustive search in exact rational arithmetic; F <= 1 accelerates
+    nothing and F >= F_W everything."""
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        T = int(rng.integers(1, 400))
+        fw = float(rng.uniform(1.05, 3.0))
+        F = float(rng.uniform(1.0, fw))
+        k = orc.kernels_for_throughput(T, F, fw)
+        Fq, fwq = Fraction(F), Fraction(fw)
+        ok = [Fraction(T) / ((T - j) + Fraction(j) / fwq) >= Fq for j in range(T + 1)]
+        assert k == ok.index(True), (T, F, fw)
+    assert orc.kernels_for_throughput(50, 1.0, 1.6) == 0
+    assert orc.kernels_for_throughput(50, 0.5, 1.6) == 0
+    assert orc.kernels_for_throughput(50, 1.6, 1.6) == 50
+    assert orc.kernels_for_throughput(50, 2.0, 1.6) == 50
+    assert orc.kernels_for_throughput(50, 1.5, 0.9) == 0
+
+
+def test_throughput_control_endpoints_and_fraction_equivalence(orc):
+    """Throughput mode selects like the fraction mode with k / T: F = 1 gives
+    the conventional product bit for bit, F = F_W the uncontrolled packed
+    product, and in between the mask is the fraction mask of the same count
+    with the predicted acceleration at or above F."""
+    L = 64
+    A = synth.blockwise_crest((192, 256), 47, L, np.float64)
+    B = synth.blockwise_crest((256, 320), 48, L, np.float64)
+    kw = dict(L=L, W=3, dtype="f64", form="sym", bits=9)
+    fw = {3: 1.9}
+    full = orc.tdgemm(A, B, **kw)
+    r1 = orc.tdgemm(A, B, kernel_control=("throughput", 1.0, fw), **kw)
+    assert np.array_equal(r1.C.view(np.uint8), orc.gemm_plain(A, B, "f64").view(np.uint8))
+    rW = orc.tdgemm(A, B, kernel_control=("throughput", 1.9, fw), **kw)
+    assert np.array_equal(rW.C.view(np.uint8), full.C.view(np.uint8))
+    T = 3 * 5
+    for F in (1.2, 1.45, 1.7):
+        r = orc.tdgemm(A, B, kernel_control=("throughput", F, fw), **kw)
+        m = r.plan.extra["kernel_mask"]
+        k = int(m.sum())
+        assert T / ((T - k) + k / 1.9) >= F
+        assert k == 0 or T / ((T - k + 1) + (k - 1) / 1.9) < F
+        rf = orc.tdgemm(A, B, kernel_control=("fraction", k / T), **kw)
+        assert np.array_equal(m, rf.plan.extra["kernel_mask"])
+        assert np.array_equal(r.C.view(np.uint8), rf.C.view(np.uint8))
+
+
 # ------------------------------------------------------------------ pair-exact companders (eq. 26)
 def test_pair_exact_equals_separable_when_blocks_agree(orc):
     """Every block of A alike (and every block of B alike): each pair's
