@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "tdg_common.cuh"
@@ -31,6 +32,21 @@ static tdg_status fail(tdg_status st, const char *fmt, ...) {
 
 // lets other translation units report through tdgemm_last_error()
 void tdg::record_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+int tdg::device_sms() {
+    static std::mutex mu;
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!sms[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+        sms[dev] = n;
+    }
+    return sms[dev];
+}
 
 #define CU_TRY(expr)                                                                  \
     do {                                                                              \
@@ -476,7 +492,22 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
         p->stab_dirty = false;
     }
     const bool nA = p->tA == 'N', nB = p->tB == 'N';
-    if (p->form != TDG_PLAIN && p->mode != MODE_MANUAL) {
+    // tensor-core forms whose compander is gamma / max|x| of the block alone:
+    // statistics, companders and codes in one pass over each input
+    const bool tc_fused = is_tc_form(p->form) && p->mode == MODE_FIXED && p->L <= 128 &&
+                          p->L % 64 == 0;
+    if (tc_fused) {
+        if constexpr (sizeof(T) == 4) {
+            const long long ldk = round_up(p->K, 128);
+            const int fp8 = p->form == TDG_TC_FP8;
+            const double gamma = fp8 ? kFp8Max : (double)((1 << (p->bits - 1)) - 1);
+            PackOperand<float> oa = operand_A<float>(p, A, nullptr);
+            PackOperand<float> ob = operand_B<float>(p, B, nullptr);
+            CU_TRY(launch_codes_stats(oa, p->mA, p->eA, (float *)p->cA, p->sA, p->Abuf,
+                                      reuse_b ? nullptr : &ob, p->mB, p->eB, (float *)p->cB,
+                                      p->sB, p->Bbuf, fp8, gamma, ldk, p->dplan, st));
+        }
+    } else if (p->form != TDG_PLAIN && p->mode != MODE_MANUAL) {
         // stats of op(A): stored rows x cols; op block grid nM x nK
         CU_TRY(launch_block_stats<T>(A, nA ? p->M : p->K, nA ? p->K : p->M, p->lda, nA ? 0 : 1,
                                      p->nK, p->mA, p->eA, B, reuse_b ? 0 : (nB ? p->K : p->N),
@@ -486,7 +517,7 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
     PlanParams pp = params_of(p);
     const double *stab = p->have_table ? p->stab : nullptr;
     CU_TRY(launch_planner<T>(pp, p->mA, p->eA, p->mB, p->eB, stab, p->dplan, p->agg, (T *)p->cA,
-                             p->sA, (T *)p->cB, p->sB, (T *)p->pair, st));
+                             p->sA, (T *)p->cB, p->sB, (T *)p->pair, st, tc_fused));
     const bool px = (p->flags & TDG_PAIR_EXACT) != 0;
     if (px)
         CU_TRY(launch_px_scales<T>(pp, p->mA, p->eA, p->mB, p->eB, p->dplan, (T *)p->cApx,
@@ -513,12 +544,15 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
     }
     if (is_tc_form(p->form)) {
         if constexpr (sizeof(T) == 4) {
-            const long long ldk = round_up(p->K, 128);
-            const int fp8 = p->form == TDG_TC_FP8;
-            CU_TRY(launch_codes(operand_A<float>(p, A, (const float *)p->cA), fp8, p->Abuf, ldk, st));
-            if (!reuse_b)
-                CU_TRY(launch_codes(operand_B<float>(p, B, (const float *)p->cB), fp8, p->Bbuf, ldk,
-                                    st));
+            if (!tc_fused) {       // (the fused path wrote the codes with the statistics)
+                const long long ldk = round_up(p->K, 128);
+                const int fp8 = p->form == TDG_TC_FP8;
+                CU_TRY(launch_codes(operand_A<float>(p, A, (const float *)p->cA), fp8, p->Abuf,
+                                    ldk, st));
+                if (!reuse_b)
+                    CU_TRY(launch_codes(operand_B<float>(p, B, (const float *)p->cB), fp8,
+                                        p->Bbuf, ldk, st));
+            }
         }
     } else {
         for (int w : candidates(p)) {

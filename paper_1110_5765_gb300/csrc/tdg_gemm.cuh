@@ -645,8 +645,8 @@ cudaError_t launch_grid(const GemmArgs<T> &g0, const GemmOperands &ops, cudaStre
         g.groups = 1;
     }
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    return launch_pdl(kern, dim3((unsigned)nblocks), dim3(Cfg::NT), Cfg::SMEM, st, ma, mb, mpa, mpb,
-                      g);
+    return launch_pdl_if(pdl_for_grid(nblocks), kern, dim3((unsigned)nblocks), dim3(Cfg::NT),
+                         Cfg::SMEM, st, ma, mb, mpa, mpb, g);
 }
 
 // KEEP (store every packed slab result for tdgemm_unpack) and MIX (Sec. 6

@@ -39,11 +39,13 @@ cudaError_t launch_block_stats(const T *A, long long rows_a, long long cols_a, l
 // candidate (W, level)), the
 // choice of W / z / companders into *plan, then c, s per block and the
 // de-companding factors.
+// scales_done: c and s per block were already written (the fused tensor-core
+// path), so the compander kernel is not launched.
 template <typename T>
 cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double *eA,
                            const double *mB, const double *eB, const double *stab,
                            DevPlan *plan, double *agg, T *cA, double *sA, T *cB, double *sB,
-                           T *pair, cudaStream_t st);
+                           T *pair, cudaStream_t st, bool scales_done = false);
 
 // Launch order of the tiles of a mixed (Sec. 6) launch: the tiles of
 // unaccelerated inner kernels first, then the accelerated ones, each group in
@@ -82,6 +84,16 @@ cudaError_t launch_pack_x(const PackOperand<T> &o, int W, const DevPlan *plan, i
 
 cudaError_t launch_codes(const PackOperand<float> &o, int fp8, void *out, long long ldo,
                          cudaStream_t st);
+
+// Tensor-core forms whose compander depends only on the block's own maximum
+// (c = gamma / max|x|: fixed bits, or gamma = 448 for E4M3): statistics,
+// companders (c in fp32, s = 1/c in fp64) and codes of op(A) and, when b is
+// given, op(B) in one launch reading each input once.  L in {64, 128}.
+cudaError_t launch_codes_stats(const PackOperand<float> &a, double *mxA, double *varA,
+                               float *cA, double *sA, void *outA, const PackOperand<float> *b,
+                               double *mxB, double *varB, float *cB, double *sB, void *outB,
+                               int fp8, double gamma, long long ldo, DevPlan *plan,
+                               cudaStream_t st);
 
 // Arguments of the CUDA-core packed GEMM (steps c and d).
 template <typename T>

@@ -452,6 +452,192 @@ __global__ void __launch_bounds__(256) codes_xc_kernel(Src<float> S, unsigned ch
     }
 }
 
+// ------------------------------------------------------------------ fused statistics + codes
+// The tensor-core forms with companders that depend only on the block's own
+// maximum (fixed bits: c = gamma / max|x|; E4M3: c = 448 / max|x|): one CTA
+// per L x L block of op(X) (L <= 128) reads the block once, keeps it in
+// registers, reduces max|x| (exact) and sum x^2 (double-float, as the
+// statistics kernel does), sets c (fp64, rounded to fp32) and s = 1/c, and
+// writes the block's codes out[x][k] -- the statistics pass, the compander
+// kernel and the code pass of the general path in one read of the input.
+struct FusedOp {
+    Src<float> S;
+    long long nbx, nbk;             // blocks along x and k
+    double *mx, *var;               // per block, index bi * S.cx + bk * S.cl
+    float *c;
+    double *s;
+    unsigned char *out;
+};
+
+__device__ inline void df_add2(float &hi, float &lo, float bh, float bl) {
+    const float s = __fadd_rn(hi, bh);
+    const float v = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(bh, v));
+    const float t = __fadd_rn(e, __fadd_rn(lo, bl));
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// exact square as hi + err (TwoProduct), TwoSum into (hi, lo)
+__device__ inline void df_add_sq(float &hi, float &lo, float x) {
+    const float p = __fmul_rn(x, x);
+    const float e = __fmaf_rn(x, x, -p);
+    const float t = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+constexpr int kFusedThreads = 256;
+
+// block statistics of the values this thread holds, reduced over the CTA;
+// thread 0 writes them with the compander, every thread returns c
+template <int NVAL>
+__device__ inline float fused_block_companders(const float (&v)[NVAL], const FusedOp &o,
+                                               long long bx, long long bk, int xn, int kn,
+                                               double gamma, DevPlan *plan) {
+    __shared__ float red_h[32], red_l[32];
+    __shared__ unsigned int red_m[32];
+    __shared__ int red_b[32];
+    __shared__ float c_sh;
+    float hi = 0.f, lo = 0.f;
+    unsigned int mb = 0;
+    int bad = 0;
+#pragma unroll
+    for (int u = 0; u < NVAL; ++u) {
+        const unsigned int b = __float_as_uint(v[u]) & 0x7fffffffu;
+        mb = max(mb, b);
+        bad |= (b >= 0x7f800000u);
+        df_add_sq(hi, lo, v[u]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto warp_reduce = [&]() {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
+            const float ol = __shfl_xor_sync(0xffffffffu, lo, off);
+            df_add2(hi, lo, oh, ol);
+            mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+            bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+        }
+    };
+    warp_reduce();
+    if (lane == 0) { red_h[warp] = hi; red_l[warp] = lo; red_m[warp] = mb; red_b[warp] = bad; }
+    __syncthreads();
+    if (warp == 0) {
+        const bool in = lane < kFusedThreads / 32;
+        hi = in ? red_h[lane] : 0.f;
+        lo = in ? red_l[lane] : 0.f;
+        mb = in ? red_m[lane] : 0u;
+        bad = in ? red_b[lane] : 0;
+        warp_reduce();
+        if (lane == 0) {
+            const double m = (double)__uint_as_float(mb);
+            const long long idx = bx * o.S.cx + bk * o.S.cl;
+            // eq. 3's compander: c = gamma / max|x| in fp64, rounded to fp32
+            const double c = m > 0.0 ? __ddiv_rn(gamma, m) : 0.0;
+            o.mx[idx] = m;
+            o.var[idx] = ((double)hi + (double)lo) / ((double)xn * (double)kn);
+            o.c[idx] = (float)c;
+            o.s[idx] = c > 0.0 ? __ddiv_rn(1.0, c) : 0.0;
+            c_sh = (float)c;
+            if (bad) atomicExch(&plan->nonfinite, 1);
+        }
+    }
+    __syncthreads();
+    return c_sh;
+}
+
+template <int FP8, int L>
+__global__ void __launch_bounds__(kFusedThreads)
+    codes_stats_kernel(FusedOp A, FusedOp B, long long nblkA, double gamma, long long ldo,
+                       DevPlan *plan) {
+    pdl_entry();
+    constexpr int ES = FP8 ? 1 : 2;
+    constexpr int NV = L * L / kFusedThreads;    // values per thread: 64 at L = 128
+    extern __shared__ float s_tile[];            // x-contiguous inputs: s[k][x], pitch L + 1
+    const bool isA = (long long)blockIdx.x < nblkA;
+    const FusedOp &o = isA ? A : B;
+    const long long blk = isA ? (long long)blockIdx.x : (long long)blockIdx.x - nblkA;
+    const long long bx = blk / o.nbk, bk = blk - bx * o.nbk;
+    const Src<float> &S = o.S;
+    const long long x0 = bx * L, k0 = bk * L;
+    const int xn = (int)min((long long)L, S.X - x0), kn = (int)min((long long)L, S.K - k0);
+    float v[NV];
+    if (S.sk == 1) {
+        // k contiguous: item = 8 consecutive k of one row x, loaded, counted
+        // and encoded by the same thread
+#pragma unroll
+        for (int u = 0; u < NV / 8; ++u) {
+            const int e = threadIdx.x + u * kFusedThreads;
+            const int xr = e / (L / 8), kr = (e % (L / 8)) * 8;
+            const float *src = S.p + (x0 + xr) * S.sx + k0 + kr;
+            const bool full = xr < xn && kr + 8 <= kn && ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
+            if (full) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(src));
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(src + 4));
+                v[8 * u] = a.x; v[8 * u + 1] = a.y; v[8 * u + 2] = a.z; v[8 * u + 3] = a.w;
+                v[8 * u + 4] = b.x; v[8 * u + 5] = b.y; v[8 * u + 6] = b.z; v[8 * u + 7] = b.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    v[8 * u + i] = (xr < xn && kr + i < kn) ? src[i] : 0.f;
+            }
+        }
+        const float c = fused_block_companders(v, o, bx, bk, xn, kn, gamma, plan);
+#pragma unroll
+        for (int u = 0; u < NV / 8; ++u) {
+            const int e = threadIdx.x + u * kFusedThreads;
+            const int xr = e / (L / 8), kr = (e % (L / 8)) * 8;
+            const long long k = k0 + kr;
+            if (xr >= xn || k >= ldo) continue;
+            float w[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[i] = __fmul_rn(v[8 * u + i], c);
+            encode8<FP8>(w, o.out + ((x0 + xr) * ldo + k) * ES);
+        }
+    } else {
+        // x contiguous: 4 consecutive x of one row k per load, transposed
+        // through shared memory for the k-contiguous codes
+        constexpr int P = L + 1;
+#pragma unroll
+        for (int u = 0; u < NV / 4; ++u) {
+            const int e = threadIdx.x + u * kFusedThreads;
+            const int kr = e / (L / 4), xr = (e % (L / 4)) * 4;
+            const float *src = S.p + (k0 + kr) * S.sk + x0 + xr;
+            const bool full = kr < kn && xr + 4 <= xn && ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
+            if (full) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(src));
+                v[4 * u] = a.x; v[4 * u + 1] = a.y; v[4 * u + 2] = a.z; v[4 * u + 3] = a.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    v[4 * u + i] = (kr < kn && xr + i < xn) ? src[i] : 0.f;
+            }
+        }
+        const float c = fused_block_companders(v, o, bx, bk, xn, kn, gamma, plan);
+#pragma unroll
+        for (int u = 0; u < NV / 4; ++u) {
+            const int e = threadIdx.x + u * kFusedThreads;
+            const int kr = e / (L / 4), xr = (e % (L / 4)) * 4;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s_tile[kr * P + xr + i] = v[4 * u + i];
+        }
+        __syncthreads();
+        // items: 8 consecutive k of one row x, lanes along x (conflict-free reads)
+        for (int e = threadIdx.x; e < L * L / 8; e += kFusedThreads) {
+            const int xr = e % L, kr = (e / L) * 8;
+            const long long k = k0 + kr;
+            if (xr >= xn || k >= ldo) continue;
+            float w[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[i] = __fmul_rn(s_tile[(kr + i) * P + xr], c);
+            encode8<FP8>(w, o.out + ((x0 + xr) * ldo + k) * ES);
+        }
+    }
+}
+
 template <typename T>
 Src<T> make_src(const PackOperand<T> &o) {
     Src<T> S;
@@ -583,6 +769,46 @@ cudaError_t launch_codes(const PackOperand<float> &o, int fp8, void *out, long l
                    : launch_pdl(codes_xc_kernel<0>, dim3(g), dim3(256), 0, st, S, ob, ldo, vec_ok);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_codes_stats(const PackOperand<float> &a, double *mxA, double *varA,
+                               float *cA, double *sA, void *outA, const PackOperand<float> *b,
+                               double *mxB, double *varB, float *cB, double *sB, void *outB,
+                               int fp8, double gamma, long long ldo, DevPlan *plan,
+                               cudaStream_t st) {
+    const int L = a.L;
+    if (L > 128 || L % 64) return cudaErrorInvalidValue;
+    auto op = [&](const PackOperand<float> &o, double *mx, double *var, float *c, double *s,
+                  void *out) {
+        FusedOp f;
+        f.S = make_src(o);
+        f.nbx = (o.X + L - 1) / L;
+        f.nbk = (o.K + L - 1) / L;
+        f.mx = mx; f.var = var; f.c = c; f.s = s;
+        f.out = reinterpret_cast<unsigned char *>(out);
+        return f;
+    };
+    FusedOp fa = op(a, mxA, varA, cA, sA, outA);
+    FusedOp fb = b ? op(*b, mxB, varB, cB, sB, outB) : fa;
+    const long long na = fa.nbx * fa.nbk, nb = b ? fb.nbx * fb.nbk : 0;
+    if (na + nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const bool xc = a.sk != 1 || (b && b->sk != 1);
+    const size_t smem = xc ? (size_t)L * (L + 1) * sizeof(float) : 0;
+    auto kern = L == 128 ? (fp8 ? codes_stats_kernel<1, 128> : codes_stats_kernel<0, 128>)
+                         : (fp8 ? codes_stats_kernel<1, 64> : codes_stats_kernel<0, 64>);
+    static std::once_flag attr_once;
+    cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [&]() {
+        // the L = 128 tile needs 66 KB of dynamic shared memory
+        for (auto k : {codes_stats_kernel<0, 128>, codes_stats_kernel<1, 128>}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(128 * 129 * sizeof(float)));
+            if (e != cudaSuccess) attr_err = e;
+        }
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    return launch_pdl(kern, dim3((unsigned)(na + nb)), dim3(kFusedThreads), smem, st, fa, fb, na,
+                      gamma, ldo, plan);
 }
 
 template cudaError_t launch_pack_k<float>(const PackOperand<float> &, int, const DevPlan *, int, int,

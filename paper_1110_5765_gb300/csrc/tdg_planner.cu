@@ -523,7 +523,7 @@ template <typename T>
 cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double *eA,
                            const double *mB, const double *eB, const double *stab,
                            DevPlan *plan, double *agg, T *cA, double *sA, T *cB, double *sB,
-                           T *pair, cudaStream_t st) {
+                           T *pair, cudaStream_t st, bool scales_done) {
     // agg: 4 nK per-slab aggregates, then one record per candidate (W, level)
     LevelRec *res = reinterpret_cast<LevelRec *>(agg + 4 * (long long)pp.nK);
     if (pp.mode != MODE_MANUAL) {
@@ -545,13 +545,15 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
     cudaError_t e = launch_pdl(planner_kernel, dim3(1), dim3(kPlanThreads), 0, st, pp,
                                (const double *)agg, stab, (const LevelRec *)res, plan);
     if (e != cudaSuccess) return e;
-    long long nblk = (long long)pp.nM * pp.nK + (long long)pp.nK * pp.nN;
-    int g = (int)min((nblk + 255) / 256, 4096LL);
-    e = launch_pdl(scales_kernel<T>, dim3(g), dim3(256), 0, st, pp, mA, mB, (const DevPlan *)plan,
-                   cA, sA, cB, sB);
-    if (e != cudaSuccess) return e;
+    if (!scales_done) {
+        long long nblk = (long long)pp.nM * pp.nK + (long long)pp.nK * pp.nN;
+        int g = (int)min((nblk + 255) / 256, 4096LL);
+        e = launch_pdl(scales_kernel<T>, dim3(g), dim3(256), 0, st, pp, mA, mB,
+                       (const DevPlan *)plan, cA, sA, cB, sB);
+        if (e != cudaSuccess) return e;
+    }
     long long np = (long long)pp.nK * pp.nM * pp.nN;
-    g = (int)min((np + 255) / 256, 8192LL);
+    int g = (int)min((np + 255) / 256, 8192LL);
     return launch_pdl(pairs_kernel<T>, dim3(g), dim3(256), 0, st, pp, (const double *)sA,
                       (const double *)sB, (const DevPlan *)plan, pair);
 }
@@ -559,10 +561,10 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
 template cudaError_t launch_planner<float>(const PlanParams &, const double *, const double *,
                                            const double *, const double *, const double *,
                                            DevPlan *, double *, float *, double *, float *,
-                                           double *, float *, cudaStream_t);
+                                           double *, float *, cudaStream_t, bool);
 template cudaError_t launch_planner<double>(const PlanParams &, const double *, const double *,
                                             const double *, const double *, const double *,
                                             DevPlan *, double *, double *, double *, double *,
-                                            double *, double *, cudaStream_t);
+                                            double *, double *, cudaStream_t, bool);
 
 }  // namespace tdg

@@ -298,7 +298,8 @@ cudaError_t launch_px_w(const GemmArgs<T> &g0, const GemmOperands &ops, cudaStre
     g.ntn = (int)((g.N + C::BN - 1) / C::BN);
     const long long ntiles = ((g.M + C::BM - 1) / C::BM) * g.ntn;
     if (ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    return launch_pdl(kern, dim3((unsigned)ntiles), dim3(Cfg::NT), Cfg::SMEM, st, ma, mb, g);
+    return launch_pdl_if(pdl_for_grid(ntiles), kern, dim3((unsigned)ntiles), dim3(Cfg::NT),
+                         Cfg::SMEM, st, ma, mb, g);
 }
 
 }  // namespace

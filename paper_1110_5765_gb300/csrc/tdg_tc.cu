@@ -448,7 +448,9 @@ static cudaError_t launch_tc(const TcArgs &a, const CUtensorMap &mapA, const CUt
     }
     const long long pairs = ((a.N + BN - 1) / BN) * (((a.M + BM - 1) / BM + 1) / 2);
     cfg.gridDim = dim3((unsigned)(2 * std::min<long long>(pairs, max_clusters)));
-    cfg.numAttrs = 2;                    // the launch: cluster shape and programmatic serialisation
+    // the launch: cluster shape, and programmatic serialisation unless the grid
+    // leaves SMs idle
+    cfg.numAttrs = pdl_for_grid(cfg.gridDim.x) ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, kern, mapA, mapB, a);
 }
 

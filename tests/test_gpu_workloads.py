@@ -56,6 +56,45 @@ def test_eigenface_covariance(tdg, orc, faces, target):
         assert same_bits(got, ref.C)
 
 
+@pytest.mark.parametrize("form,dtype,W,target", [("sym", "f64", 3, 30.0), ("sym", "f64", 3, 50.0),
+                                                  ("tc_int", "f32", 1, 30.0),
+                                                  ("tc_int", "f32", 1, 50.0)])
+def test_eigenface_covariance_packed_paths(tdg, orc, faces, form, dtype, W, target):
+    """The eigenface covariance C = X^T X (4096 x 4096 x 10304) through the
+    paths that reach 30-50 dB where fp32 packing cannot: fp64 symmetric
+    packing (the planner choosing W <= 3) and the tensor-core integer form.
+    Plan decisions and two sampled 128 x 128 tiles equal the oracle's; the
+    tensor-core form reports TDG_EUNREACHABLE exactly when the oracle's
+    predicted SNR misses the target (its widest exact companders still run)."""
+    T = np.float64 if dtype == "f64" else np.float32
+    X = faces.astype(T)
+    Xd = torch.from_numpy(X).cuda()
+    p = tdg.Plan(4096, 4096, 10304, L=128, W=W, dtype=dtype, form=form, target_snr_db=target,
+                 transA="T", lda=4096)
+    C = p.run(Xd, Xd)
+    torch.cuda.synchronize()
+    info = p.info()
+    p.close()
+    A_op = np.ascontiguousarray(X.T)
+    st = orc.load_s_table()
+    for k, (ti, tj) in enumerate(synth.sample_tiles(32, 32, 2, seed=int(target) + 7)):
+        rows, cols = (ti * 128, ti * 128 + 128), (tj * 128, tj * 128 + 128)
+        if form == "tc_int":
+            ref = orc.tc_int_gemm(A_op, X, L=128, bits=0, rows=rows, cols=cols)
+            want_status = 0 if ref.plan.pred_snr_db >= target else 5
+            assert info["device_status"] == want_status, (info, ref.plan.pred_snr_db)
+            assert (info["gamma_a"], info["gamma_b"]) == (ref.plan.gA, ref.plan.gB)
+        else:
+            ref = orc.tdgemm(A_op, X, L=128, W=W, dtype=dtype, form="sym", target_db=target,
+                             s_table=st, rows=rows, cols=cols)
+            assert info["device_status"] == 0, info
+            assert (info["W_used"], info["q"], info["gamma_a"], info["gamma_b"]) == \
+                (ref.plan.W, ref.plan.q, ref.plan.gA, ref.plan.gB)
+            assert ref.plan.W >= 2          # packed, not the conventional fallback
+        got = C[rows[0]:rows[1], cols[0]:cols[1]].cpu().numpy()
+        assert same_bits(got, ref.C), (ti, tj)
+
+
 def test_eigenface_projection(tdg, orc, faces):
     """Y = X^T U onto 400 orthonormal columns (N = 400 is a ragged 3.1 blocks),
     fp32 symmetric W = 2 at 30 dB: sampled tiles equal the oracle's."""
