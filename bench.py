@@ -882,9 +882,7 @@ def fig6_study(out_path=None, ftab=None):
     fw = (ftab if isinstance(ftab, dict) else tdg.api.load_speedups()).get(
         f"f32/sym/W2/L{L_BLOCK}", {}).get("F")
     if fw:
-        for F in sorted({1.0, 1.1, 1.2, 1.3, 1.4, 1.5, round(fw, 3)}):
-            if F > fw:
-                continue
+        for F in sorted({F for F in (1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6) if F < fw} | {fw}):
             p.set_kernel_control("throughput", F)
             t, tg = _time_split(p, A32, B32, C, torch, reps=3)
             mask = p.kernel_mask()
