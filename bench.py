@@ -322,12 +322,12 @@ def run_reference(args):
 def launches_per_step(plan) -> int:
     """Kernels this library queues per tdgemm_run for a target-mode symmetric
     fp32 plan with fallback, inputs 'N'/'N': block statistics of A and B (one
-    launch), planner (per-slab aggregates, per-candidate records, selection),
-    companders and de-companding factors, pack A and B for W = 2, plain copy
-    of A for the W = 1 fallback (B is used in place), packed GEMM for W = 2 and
-    plain GEMM for the fallback (kernels not chosen by the planner exit at
-    entry).  Counted from the ncu launch list of one step."""
-    return 1 + 3 + 2 + 2 + 1 + 2
+    launch), planner (per-slab aggregates; every candidate level, the last CTA
+    deciding the plan), companders and de-companding factors, pack A and B for
+    W = 2, plain copy of A for the W = 1 fallback (B is used in place), packed
+    GEMM for W = 2 and plain GEMM for the fallback (kernels not chosen by the
+    planner exit at entry).  Counted from the ncu launch list of one step."""
+    return 1 + 2 + 2 + 2 + 1 + 2
 
 
 def run_gpu(args):

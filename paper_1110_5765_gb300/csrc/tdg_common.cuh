@@ -33,7 +33,42 @@ struct DevPlan {
     double pred_snr;   // model SNR (dB), NaN if not modelled
     double s_rep;      // representation-noise RMSE the model used (0 if none)
     double S, T1, T2, T3;  // noise-model aggregates
+    unsigned int levels_done;  // candidate-level CTAs finished (the last one decides)
 };
+
+// Per-slab aggregates X_l = sum_i sigma_A,il^2, MA_l = sum_i m_A,il^2,
+// Y_l = sum_j sigma_B,lj^2, MB_l = sum_j m_B,lj^2 of slab l, written to
+// agg[4 l .. 4 l + 3] by one warp: lanes over i (j), then a fixed xor tree.
+__device__ inline void slab_aggregate_warp(int l, int nM, int nK, int nN,
+                                           const double *mA, const double *vA,
+                                           const double *mB, const double *vB, double *agg) {
+    const int lane = threadIdx.x & 31;
+    double X = 0, MA = 0, Y = 0, MB = 0;
+    for (int i = lane; i < nM; i += 32) {
+        X += vA[(long long)i * nK + l];
+        const double m = mA[(long long)i * nK + l];
+        MA += m * m;
+    }
+    for (int j = lane; j < nN; j += 32) {
+        Y += vB[(long long)l * nN + j];
+        const double m = mB[(long long)l * nN + j];
+        MB += m * m;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        X += __shfl_xor_sync(0xffffffffu, X, off);
+        MA += __shfl_xor_sync(0xffffffffu, MA, off);
+        Y += __shfl_xor_sync(0xffffffffu, Y, off);
+        MB += __shfl_xor_sync(0xffffffffu, MB, off);
+    }
+    if (lane == 0) {
+        agg[4 * (long long)l + 0] = X;
+        agg[4 * (long long)l + 1] = MA;
+        agg[4 * (long long)l + 2] = Y;
+        agg[4 * (long long)l + 3] = MB;
+    }
+}
+
 
 // Planner inputs that do not change between calls.
 struct PlanParams {

@@ -23,7 +23,6 @@ namespace tdg {
 
 namespace {
 
-constexpr int kPlanThreads = 256;
 
 // The plain product (form PLAIN, or the W = 1 fallback of target mode for the
 // packed forms) uses no companders.
@@ -58,11 +57,9 @@ __device__ inline double snr_db(double S, double N) {
     return N <= 0.0 ? INFINITY : 10.0 * log10(S / N);
 }
 
-// Per-slab aggregates X_l = sum_i sigma_A,il^2, MA_l = sum_i m_A,il^2,
-// Y_l = sum_j sigma_B,lj^2, MB_l = sum_j m_B,lj^2: one warp per slab on its own
-// SM (GB300's fp64 rate is a small fraction of fp32, so the sums are spread
-// over the GPU rather than serialised on one SM), lanes over i (j), then a
-// fixed xor tree.
+// Per-slab aggregates (slab_aggregate_warp): one warp per slab on its own SM
+// (GB300's fp64 rate is a small fraction of fp32, so the sums are spread over
+// the GPU rather than serialised on one SM).
 __global__ void __launch_bounds__(32) slab_aggregates_kernel(PlanParams pp,
                                                              const double *__restrict__ mA,
                                                              const double *__restrict__ vA,
@@ -71,31 +68,7 @@ __global__ void __launch_bounds__(32) slab_aggregates_kernel(PlanParams pp,
                                                              double *__restrict__ agg) {
     pdl_entry();
     if (pp.mode == MODE_MANUAL) return;
-    const int l = blockIdx.x, lane = threadIdx.x;
-    double X = 0, MA = 0, Y = 0, MB = 0;
-    for (int i = lane; i < pp.nM; i += 32) {
-        X += vA[(long long)i * pp.nK + l];
-        const double m = mA[(long long)i * pp.nK + l];
-        MA += m * m;
-    }
-    for (int j = lane; j < pp.nN; j += 32) {
-        Y += vB[(long long)l * pp.nN + j];
-        const double m = mB[(long long)l * pp.nN + j];
-        MB += m * m;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        X += __shfl_xor_sync(0xffffffffu, X, off);
-        MA += __shfl_xor_sync(0xffffffffu, MA, off);
-        Y += __shfl_xor_sync(0xffffffffu, Y, off);
-        MB += __shfl_xor_sync(0xffffffffu, MB, off);
-    }
-    if (lane == 0) {
-        agg[4 * (long long)l + 0] = X;
-        agg[4 * (long long)l + 1] = MA;
-        agg[4 * (long long)l + 2] = Y;
-        agg[4 * (long long)l + 3] = MB;
-    }
+    slab_aggregate_warp((int)blockIdx.x, pp.nM, pp.nK, pp.nN, mA, vA, mB, vB, agg);
 }
 
 // S / L, T1, T2, T3: products of the per-slab aggregates summed over slabs by
@@ -140,65 +113,37 @@ struct LevelRec {
 };
 static_assert(sizeof(LevelRec) == kLevelRecDoubles * sizeof(double), "planner workspace record");
 
-__global__ void __launch_bounds__(32) level_kernel(PlanParams pp, const double *__restrict__ agg,
-                                                   const double *__restrict__ stab,
-                                                   LevelRec *__restrict__ res) {
-    pdl_entry();
-    const int L = pp.L;
-    int t_lo = 0;
-    while (r_level(t_lo) < L) ++t_lo;
-    const int t_hi = t_max_for(pp.p);
-    const int nlev = t_hi - t_lo + 1;
-    const int per_w = (nlev + 31) / 32;                 // CTAs per W
-    const int W = pp.Wreq - (int)blockIdx.x / per_w;
-    const int t = t_lo + ((int)blockIdx.x % per_w) * 32 + (int)threadIdx.x;
-    DevPlan a{};
-    double S, T1, T2, T3;
-    slab_totals(pp, agg, S, T1, T2, T3);
-    if (W < 2 || t > t_hi) return;
-    a.S = (double)L * S; a.T1 = T1; a.T2 = T2; a.T3 = T3;
-    const double rho = rho_of(T1, T2);
-    LevelRec r{};
-    r.n = -1.0;
-    const long long Rt = r_level(t);
-    r.q = q_for(Rt);
-    split_gammas(Rt, L, rho, r.gA, r.gB);
-    if (r.gA >= 1) {
-        r.R = (long long)L * r.gA * r.gB;
-        r.Wef = w_ef(r.R, r.q, pp.p);
-        double sv = -1.0;
-        if (W <= r.Wef) sv = 0.0;
-        else if (stab && t >= pp.t0 && t < pp.t0 + pp.nt) sv = stab[(W - 2) * pp.nt + (t - pp.t0)];
-        if (sv >= 0.0) {
-            r.n = model_noise(a, L, r.gA, r.gB, sv, pp.noise_rms);
-            r.pred = snr_db(a.S, r.n);
-            r.s = sv > 0.0 ? sv : 0.0;
-        }
-    }
-    res[(W - 2) * kMaxLevels + t] = r;
+// a candidate record written by another CTA of the same grid: read from L2
+__device__ inline LevelRec load_rec(const LevelRec *p) {
+    LevelRec r;
+    r.n = __ldcg(&p->n);
+    r.pred = __ldcg(&p->pred);
+    r.s = __ldcg(&p->s);
+    r.R = __ldcg(&p->R);
+    r.gA = __ldcg(&p->gA);
+    r.gB = __ldcg(&p->gB);
+    r.q = __ldcg(&p->q);
+    r.Wef = __ldcg(&p->Wef);
+    return r;
 }
 
-__global__ void __launch_bounds__(kPlanThreads) planner_kernel(
-    PlanParams pp, const double *__restrict__ agg, const double *__restrict__ stab,
-    const LevelRec *__restrict__ res, DevPlan *plan) {
-    pdl_entry();
-    __shared__ unsigned long long best_n[kPlanThreads];
-    __shared__ int best_t[kPlanThreads];
-    __shared__ double tot[4];
-    const int tid = threadIdx.x;
+// The plan, decided by one full warp: fixed bits, manual parameters, the
+// tensor-core forms, or (target mode, packed forms) the choice among the
+// candidate records res: for W from the request down to 2 the level of least
+// model noise (eq. 27's argmax of the SNR; ties to the lower level), the first
+// W whose SNR meets the target; else the plain product (fallback) or
+// TDG_EUNREACHABLE.  Lane 0 writes the plan.
+__device__ void decide_plan(const PlanParams &pp, const double *__restrict__ agg,
+                            const double *__restrict__ stab, const LevelRec *res, DevPlan *plan) {
+    const int lane = threadIdx.x & 31;
     const int L = pp.L;
-
-    if (tid < 32) {
-        double S, T1, T2, T3;
-        slab_totals(pp, agg, S, T1, T2, T3);
-        if (tid == 0) { tot[0] = S; tot[1] = T1; tot[2] = T2; tot[3] = T3; }
-    }
-    __syncthreads();
-    DevPlan a;
-    a.S = (double)L * tot[0];
-    a.T1 = tot[1];
-    a.T2 = tot[2];
-    a.T3 = tot[3];
+    double S, T1, T2, T3;
+    slab_totals(pp, agg, S, T1, T2, T3);
+    DevPlan a{};
+    a.S = (double)L * S;
+    a.T1 = T1;
+    a.T2 = T2;
+    a.T3 = T3;
     const double rho = rho_of(a.T1, a.T2);
     a.status = 0;
     a.level = -1;
@@ -252,33 +197,34 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
         for (int W = pp.Wreq; W >= 2 && !chosen; --W) {
             // argmin of N over the levels (ties to the lower level); N >= 0,
             // so its bit pattern orders like its value (integer compares)
+            // every load of the lane's levels issued before any is used
+            constexpr int kPerLane = (kMaxLevels + 31) / 32;
+            double nv[kPerLane];
+#pragma unroll
+            for (int u = 0; u < kPerLane; ++u) {
+                const int t = t_lo + lane + 32 * u;
+                nv[u] = t <= t_hi ? __ldcg(&res[(W - 2) * kMaxLevels + t].n) : -1.0;
+            }
             unsigned long long bn = ~0ull;
             int bt = -1;
-            for (int t = t_lo + tid; t <= t_hi; t += kPlanThreads) {
-                const double n = res[(W - 2) * kMaxLevels + t].n;   // level_kernel
-                if (n < 0.0) continue;
-                const unsigned long long nb = (unsigned long long)__double_as_longlong(n);
-                if (nb < bn) { bn = nb; bt = t; }
+#pragma unroll
+            for (int u = 0; u < kPerLane; ++u) {     // lanes scan ascending t
+                if (nv[u] < 0.0) continue;
+                const unsigned long long nb = (unsigned long long)__double_as_longlong(nv[u]);
+                if (nb < bn) { bn = nb; bt = t_lo + lane + 32 * u; }
             }
-            best_n[tid] = bn;
-            best_t[tid] = bt;
-            __syncthreads();
-            for (int o = kPlanThreads / 2; o > 0; o >>= 1) {
-                if (tid < o) {
-                    const unsigned long long n2 = best_n[tid + o];
-                    const int t2 = best_t[tid + o];
-                    if (t2 >= 0 && (best_t[tid] < 0 || n2 < best_n[tid] ||
-                                    (n2 == best_n[tid] && t2 < best_t[tid]))) {
-                        best_n[tid] = n2;
-                        best_t[tid] = t2;
-                    }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long n2 = __shfl_xor_sync(0xffffffffu, bn, off);
+                const int t2 = __shfl_xor_sync(0xffffffffu, bt, off);
+                if (t2 >= 0 && (bt < 0 || n2 < bn || (n2 == bn && t2 < bt))) {
+                    bn = n2;
+                    bt = t2;
                 }
-                __syncthreads();
             }
-            const int t = best_t[0];
-            __syncthreads();
+            const int t = bt;                          // the same in every lane
             if (t < 0) continue;
-            const LevelRec &r = res[(W - 2) * kMaxLevels + t];
+            const LevelRec r = load_rec(&res[(W - 2) * kMaxLevels + t]);
             DevPlan c = a;
             c.W = W;
             c.q = r.q;
@@ -305,12 +251,77 @@ __global__ void __launch_bounds__(kPlanThreads) planner_kernel(
             }
         }
     }
-    if (tid == 0) {
-        int nf = plan->nonfinite;
+    if (lane == 0) {
+        const int nf = __ldcg(&plan->nonfinite);
         a.nonfinite = nf;
         if (nf && a.status == 0) a.status = TDG_ENONFINITE;
         *plan = a;
     }
+}
+
+// Target mode, packed forms: each lane evaluates one candidate (W, R_max
+// level t) in full -- companders, z, representation noise, model noise and
+// SNR -- 32 candidates per CTA spread over SMs (fp64 divisions, square roots
+// and logarithms are slow on GB300 and would serialise on one SM).  The last
+// CTA to finish (a counter in the plan, no waiting) then decides the plan
+// from all records.  n < 0 marks a level without usable companders or
+// representation-noise value.
+__global__ void __launch_bounds__(32) level_kernel(PlanParams pp, const double *__restrict__ agg,
+                                                   const double *__restrict__ stab,
+                                                   LevelRec *res, DevPlan *plan) {
+    pdl_entry();
+    const int L = pp.L;
+    const int lane = threadIdx.x;
+    int t_lo = 0;
+    while (r_level(t_lo) < L) ++t_lo;
+    const int t_hi = t_max_for(pp.p);
+    const int nlev = t_hi - t_lo + 1;
+    const int per_w = (nlev + 31) / 32;                 // CTAs per W
+    const int W = pp.Wreq - (int)blockIdx.x / per_w;
+    const int t = t_lo + ((int)blockIdx.x % per_w) * 32 + lane;
+    double S, T1, T2, T3;
+    slab_totals(pp, agg, S, T1, T2, T3);
+    if (W >= 2 && t <= t_hi) {
+        DevPlan a{};
+        a.S = (double)L * S; a.T1 = T1; a.T2 = T2; a.T3 = T3;
+        const double rho = rho_of(T1, T2);
+        LevelRec r{};
+        r.n = -1.0;
+        const long long Rt = r_level(t);
+        r.q = q_for(Rt);
+        split_gammas(Rt, L, rho, r.gA, r.gB);
+        if (r.gA >= 1) {
+            r.R = (long long)L * r.gA * r.gB;
+            r.Wef = w_ef(r.R, r.q, pp.p);
+            double sv = -1.0;
+            if (W <= r.Wef) sv = 0.0;
+            else if (stab && t >= pp.t0 && t < pp.t0 + pp.nt) sv = stab[(W - 2) * pp.nt + (t - pp.t0)];
+            if (sv >= 0.0) {
+                r.n = model_noise(a, L, r.gA, r.gB, sv, pp.noise_rms);
+                r.pred = snr_db(a.S, r.n);
+                r.s = sv > 0.0 ? sv : 0.0;
+            }
+        }
+        res[(W - 2) * kMaxLevels + t] = r;
+    }
+    // the records of this CTA are written: count it; the last one decides
+    __threadfence();
+    __syncwarp();
+    unsigned int prev = 0;
+    if (lane == 0) prev = atomicAdd(&plan->levels_done, 1u);
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev + 1 == gridDim.x) {
+        __threadfence();
+        decide_plan(pp, agg, stab, res, plan);
+    }
+}
+
+// The plan for every mode but the packed forms' target mode (one warp).
+__global__ void __launch_bounds__(32) planner_kernel(PlanParams pp, const double *__restrict__ agg,
+                                                     const double *__restrict__ stab,
+                                                     const LevelRec *res, DevPlan *plan) {
+    pdl_entry();
+    decide_plan(pp, agg, stab, res, plan);
 }
 
 // c = gamma / max|x| (fp64, rounded to T for eq. 3), s = 1/c, per block.
@@ -531,19 +542,19 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
             launch_pdl(slab_aggregates_kernel, dim3(pp.nK), dim3(32), 0, st, pp, mA, eA, mB, eB, agg);
         if (e0 != cudaSuccess) return e0;
     }
+    cudaError_t e;
     if (pp.mode == MODE_TARGET && (pp.form == TDG_SYM || pp.form == TDG_ASYM)) {
+        // every candidate level, the plan decided by the last CTA to finish
         int t_lo = 0;
         while (r_level(t_lo) < pp.L) ++t_lo;
         const int nlev = (pp.p == 24 ? 4 * 24 : 4 * 40) - t_lo + 1;
-        const int ctas = (pp.Wreq - 1) * ((nlev + 31) / 32);
-        if (ctas > 0) {
-            cudaError_t e1 = launch_pdl(level_kernel, dim3(ctas), dim3(32), 0, st, pp,
-                                        (const double *)agg, stab, res);
-            if (e1 != cudaSuccess) return e1;
-        }
+        const int ctas = max(1, (pp.Wreq - 1) * ((nlev + 31) / 32));
+        e = launch_pdl(level_kernel, dim3(ctas), dim3(32), 0, st, pp, (const double *)agg, stab,
+                       res, plan);
+    } else {
+        e = launch_pdl(planner_kernel, dim3(1), dim3(32), 0, st, pp, (const double *)agg, stab,
+                       (const LevelRec *)res, plan);
     }
-    cudaError_t e = launch_pdl(planner_kernel, dim3(1), dim3(kPlanThreads), 0, st, pp,
-                               (const double *)agg, stab, (const LevelRec *)res, plan);
     if (e != cudaSuccess) return e;
     if (!scales_done) {
         long long nblk = (long long)pp.nM * pp.nK + (long long)pp.nK * pp.nN;

@@ -130,7 +130,8 @@ tdg_status run_static(bool nA, bool nB, long long M, long long N, long long K, l
     T *cA = (T *)(ws + o_cA), *cB = (T *)(ws + o_cB), *pair = (T *)(ws + o_pair);
     T *Abuf = (T *)(ws + o_A), *Bbuf = (T *)(ws + o_B);
 
-    // the plan record carries the device status and non-finite flag: start at zero
+    // the plan record carries the device status, the non-finite flag and the
+    // planner's counter: start at zero
     ST_TRY(cudaMemsetAsync(dplan, 0, sizeof(DevPlan), st));
     ST_TRY(launch_block_stats<T>(A, nA ? M : K, nA ? K : M, lda, nA ? 0 : 1, nK, mA, eA, B,
                                  nB ? K : N, nB ? N : K, ldb, nB ? 0 : 1, nN, mB, eB, L, dplan,
