@@ -661,6 +661,12 @@ static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cu
         g.alpha = (T)alpha; g.beta = (T)beta; g.beta_zero = beta == 0.0;
         g.Rbar = (!plain && (p->flags & TDG_KEEP_PACKED)) ? (T *)p->Rbar : nullptr;
         g.stall_ns = p->stall_ns;
+        if (p->mode == MODE_FIXED) {
+            const long long gam = (1LL << (p->bits - 1)) - 1;
+            g.small_t = small_t_ok(Wk, q_for((long long)p->L * gam * gam), (int)gam) ? 1 : 0;
+        } else {
+            g.small_t = p->mode == MODE_MANUAL ? 0 : -1;
+        }
         const bool split = !plain && p->split_groups > 1 && !p->kctrl_mode && p->Rbar;
         if (split) {
             g.Rbar = (T *)p->Rbar;

@@ -122,6 +122,15 @@ __host__ __device__ inline int w_ef(long long R, int q, int p) {
     return 1 + fl;
 }
 
+// The symmetric unpack's second rounding t = rint(z u) (eq. 10) may use the
+// add-subtract form exact for |x| < 2^22 when W = 2, the companders are planned
+// (|a~| <= gamma_A, |b~| <= gamma_B) and q <= 22: z u = S_01 + (R + z S_10 + e) / Q
+// with |S_01| <= R_max < Q / 2 and the rest below 2 in magnitude, so
+// |z u| < 2^21 + 2.  Manual companders bound nothing (gamma is 0 in the plan).
+__host__ __device__ inline bool small_t_ok(int W, int q, int gA) {
+    return W == 2 && q <= 22 && gA > 0;
+}
+
 // integer compander split of eq. 26 for a budget R: gA = floor(sqrt((R/L) rho))
 __device__ inline void split_gammas(long long R, int L, double rho, int &gA, int &gB) {
     long long G = R / L;

@@ -116,6 +116,17 @@ __device__ inline float rint_epi(float x) {
 #endif
 }
 __device__ inline double rint_epi(double x) { return rint(x); }
+
+// Round to nearest, ties to even, for |x| < 2^22: (x + 1.5 2^23) - 1.5 2^23 on
+// the FMA pipe (the sum lies in (2^23, 2^24), where the spacing is 1).  Equal
+// to rintf there up to the sign of a zero result, which the digit and the
+// running sum it feeds do not carry (they start at +0 and only add).  Measured
+// on GB300 in the slab epilogue: the kernel holds fewer values in flight
+// (spills 16 bytes instead of 220) and runs about 8 % faster at 4096^3.
+__device__ inline float rint_small(float x) {
+    return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+
 __device__ inline double pow2_t(double, int e) { return scalbn(1.0, e); }
 
 // ---- tensor-memory helpers (CUDA-core use of TMEM: alloc, 16-column ld/st)
@@ -214,7 +225,7 @@ struct SlabWalk {
 // the packed one.  Tiles never straddle inner kernels (L is a multiple of the
 // tile), and the block scheduler balances the two kinds of tile.
 template <typename T, int FORM, int W, int BM, int BN, int TM, int TN, int BK, int STAGES,
-          bool KEEP, bool MIX>
+          bool KEEP, bool MIX, bool SMALL_T = false>
 __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>::NT,
                                   GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES>::MIN_CTAS)
     packed_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
@@ -229,6 +240,11 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
 
     // the device planner chose another packing
     if (g.plan->W != W) return;
+    // fp32 symmetric W = 2 with both rounding variants queued: the one the
+    // plan does not select exits
+    if constexpr (sizeof(T) == 4 && FORM == G_SYM && W == 2 && !KEEP && !MIX) {
+        if (g.small_t < 0 && small_t_ok(W, g.plan->q, g.plan->gA) != SMALL_T) return;
+    }
     // this CTA's tile, row-major over ntn tiles per row; with slab splitting
     // (KEEP instantiation, groups > 1) CTA b takes tile b % ntiles and the
     // slabs of group b / ntiles
@@ -476,8 +492,13 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
                 asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t2) : "l"(z2), "l"(u2));
                 float t0, t1;
                 asm("mov.b64 {%0, %1}, %2;" : "=f"(t0), "=f"(t1) : "l"(t2));
-                t0 = rint_epi(t0);
-                t1 = rint_epi(t1);
+                if constexpr (SMALL_T) {
+                    t0 = rint_small(t0);
+                    t1 = rint_small(t1);
+                } else {
+                    t0 = rint_epi(t0);
+                    t1 = rint_epi(t1);
+                }
                 asm("mov.b64 %0, {%1, %2};" : "=l"(t2) : "f"(t0), "f"(t1));
                 asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d2) : "l"(nq2), "l"(t2), "l"(u2));  // eq. 10
                 if (slot == 0) {
@@ -605,10 +626,11 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
 }
 
 // One launch over the whole tile grid of shape C.
-template <typename T, int FORM, int W, typename C, bool KEEP, bool MIX>
+template <typename T, int FORM, int W, typename C, bool KEEP, bool MIX, bool SMALL_T = false>
 cudaError_t launch_grid(const GemmArgs<T> &g0, const GemmOperands &ops, cudaStream_t st) {
     using Cfg = GemmCfg<T, FORM, W, C::BM, C::BN, C::TM, C::TN, C::BK, C::STAGES>;
-    auto kern = packed_gemm_kernel<T, FORM, W, C::BM, C::BN, C::TM, C::TN, C::BK, C::STAGES, KEEP, MIX>;
+    auto kern = packed_gemm_kernel<T, FORM, W, C::BM, C::BN, C::TM, C::TN, C::BK, C::STAGES, KEEP,
+                                   MIX, SMALL_T>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
@@ -663,6 +685,15 @@ cudaError_t launch_cfg(const GemmArgs<T> &g, const GemmOperands &ops, cudaStream
     if (g.kmask) return cudaErrorInvalidValue;
     if (FORM != G_PLAIN && g.Rbar) return launch_grid<T, FORM, W, C, true, false>(g, ops, st);
     if (g.groups > 1) return cudaErrorInvalidValue;     // slab splitting stores r-bar
+    if constexpr (sizeof(T) == 4 && FORM == G_SYM && W == 2) {
+        // the rounding of eq. 10's t as a compile-time variant: known on the
+        // host for fixed-bit plans, else both queued and the plan picks one
+        if (g.small_t > 0) return launch_grid<T, FORM, W, C, false, false, true>(g, ops, st);
+        if (g.small_t < 0) {
+            cudaError_t e = launch_grid<T, FORM, W, C, false, false, true>(g, ops, st);
+            if (e != cudaSuccess) return e;
+        }
+    }
     return launch_grid<T, FORM, W, C, false, false>(g, ops, st);
 }
 

@@ -128,6 +128,10 @@ struct GemmArgs {
     // test of the bounded waits: > 0 makes every CTA's first wait for operand
     // tiles wait on a barrier nothing completes, giving up after this many ns
     long long stall_ns;
+    // fp32 symmetric W = 2: whether the second rounding of eq. 10 may use the
+    // add-subtract form (|z u| < 2^22, see the kernel): 1 known yes, 0 known
+    // no, -1 decided on the device (both variants queued, one runs)
+    int small_t;
 };
 
 // 2-D TMA map over a row-major [rows][cols] array with leading dimension ld

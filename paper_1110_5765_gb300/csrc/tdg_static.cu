@@ -164,6 +164,10 @@ tdg_status run_static(bool nA, bool nB, long long M, long long N, long long K, l
     g.L = L; g.P = P; g.nM = nM; g.nK = nK; g.nN = nN; g.pair = pair;
     g.C = C; g.ldc = ldc; g.alpha = (T)alpha; g.beta = (T)beta; g.beta_zero = beta == 0.0;
     g.Rbar = nullptr;
+    {
+        const long long gam = (1LL << (bits - 1)) - 1;
+        g.small_t = small_t_ok(W, q_for((long long)L * gam * gam), (int)gam) ? 1 : 0;
+    }
     ST_TRY(launch_packed_gemm<T>(gform, W, g, ops, st));
     return TDG_OK;
 }
