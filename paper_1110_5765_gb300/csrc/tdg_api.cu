@@ -663,7 +663,7 @@ static tdg_status gemm_impl(tdgemm_plan_t p, T *C, double alpha, double beta, cu
         g.stall_ns = p->stall_ns;
         if (p->mode == MODE_FIXED) {
             const long long gam = (1LL << (p->bits - 1)) - 1;
-            g.small_t = small_t_ok(Wk, q_for((long long)p->L * gam * gam), (int)gam) ? 1 : 0;
+            g.small_t = small_round_ok(gform, Wk, q_for((long long)p->L * gam * gam), (int)gam) ? 1 : 0;
         } else {
             g.small_t = p->mode == MODE_MANUAL ? 0 : -1;
         }

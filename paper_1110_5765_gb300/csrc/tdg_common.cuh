@@ -122,13 +122,21 @@ __host__ __device__ inline int w_ef(long long R, int q, int p) {
     return 1 + fl;
 }
 
-// The symmetric unpack's second rounding t = rint(z u) (eq. 10) may use the
-// add-subtract form exact for |x| < 2^22 when W = 2, the companders are planned
-// (|a~| <= gamma_A, |b~| <= gamma_B) and q <= 22: z u = S_01 + (R + z S_10 + e) / Q
-// with |S_01| <= R_max < Q / 2 and the rest below 2 in magnitude, so
-// |z u| < 2^21 + 2.  Manual companders bound nothing (gamma is 0 in the plan).
-__host__ __device__ inline bool small_t_ok(int W, int q, int gA) {
-    return W == 2 && q <= 22 && gA > 0;
+// Roundings of the unpack that may use the add-subtract form, exact for
+// |x| < 2^22, with planned companders (|a~| <= gamma_A, |b~| <= gamma_B; manual
+// companders bound nothing and leave gamma 0 in the plan) and q <= 22, so
+// R_max < Q / 2 <= 2^21:
+//   symmetric, W = 2: the second rounding t = rint(z u) of eq. 10, since
+//     z u = S_01 + (R + z S_10 + e) / Q with |S_01| <= R_max and the rest below
+//     2 in magnitude (for W > 2, z u carries powers of Q);
+//   asymmetric, any W: every rounding of eqs. 13-14, since r-bar =
+//     sum_i z^i R_i with |R_i| <= R_max, and each peeled remainder
+//     Q (r-bar_i - r~_i) is again such a sum (errors beyond the error-free
+//     region stay below Q / 2).
+__host__ __device__ inline bool small_round_ok(int form, int W, int q, int gA) {
+    if (q > 22 || gA <= 0) return false;
+    if (form == 1) return W == 2;       // symmetric (G_SYM)
+    return form == 2;                   // asymmetric (G_ASYM)
 }
 
 // integer compander split of eq. 26 for a budget R: gA = floor(sqrt((R/L) rho))

@@ -117,7 +117,8 @@ __device__ inline float rint_epi(float x) {
 }
 __device__ inline double rint_epi(double x) { return rint(x); }
 
-// Round to nearest, ties to even, for |x| < 2^22: (x + 1.5 2^23) - 1.5 2^23 on
+// Round to nearest, ties to even, for |x| < 2^22 (small_round_ok):
+// (x + 1.5 2^23) - 1.5 2^23 on
 // the FMA pipe (the sum lies in (2^23, 2^24), where the spacing is 1).  Equal
 // to rintf there up to the sign of a zero result, which the digit and the
 // running sum it feeds do not carry (they start at +0 and only add).  Measured
@@ -240,10 +241,10 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
 
     // the device planner chose another packing
     if (g.plan->W != W) return;
-    // fp32 symmetric W = 2 with both rounding variants queued: the one the
-    // plan does not select exits
-    if constexpr (sizeof(T) == 4 && FORM == G_SYM && W == 2 && !KEEP && !MIX) {
-        if (g.small_t < 0 && small_t_ok(W, g.plan->q, g.plan->gA) != SMALL_T) return;
+    // both rounding variants queued: the one the plan does not select exits
+    if constexpr (sizeof(T) == 4 && ((FORM == G_SYM && W == 2) || FORM == G_ASYM) && !KEEP &&
+                  !MIX) {
+        if (g.small_t < 0 && small_round_ok(FORM, W, g.plan->q, g.plan->gA) != SMALL_T) return;
     }
     // this CTA's tile, row-major over ntn tiles per row; with slab splitting
     // (KEEP instantiation, groups > 1) CTA b takes tile b % ntiles and the
@@ -537,7 +538,8 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
                 T x = r;
 #pragma unroll
                 for (int d = 0; d < NCACC; ++d) {               // eqs. 13-14
-                    digit[d] = rint_epi(x);
+                    if constexpr (SMALL_T) digit[d] = rint_small(x);
+                    else digit[d] = rint_epi(x);
                     if (d + 1 < NCACC) x = mul_rn(Q, sub_rn(x, digit[d]));
                 }
             }
@@ -685,9 +687,9 @@ cudaError_t launch_cfg(const GemmArgs<T> &g, const GemmOperands &ops, cudaStream
     if (g.kmask) return cudaErrorInvalidValue;
     if (FORM != G_PLAIN && g.Rbar) return launch_grid<T, FORM, W, C, true, false>(g, ops, st);
     if (g.groups > 1) return cudaErrorInvalidValue;     // slab splitting stores r-bar
-    if constexpr (sizeof(T) == 4 && FORM == G_SYM && W == 2) {
-        // the rounding of eq. 10's t as a compile-time variant: known on the
-        // host for fixed-bit plans, else both queued and the plan picks one
+    if constexpr (sizeof(T) == 4 && ((FORM == G_SYM && W == 2) || (FORM == G_ASYM && W >= 2))) {
+        // the unpack's roundings as a compile-time variant: known on the host
+        // for fixed-bit plans, else both queued and the plan picks one
         if (g.small_t > 0) return launch_grid<T, FORM, W, C, false, false, true>(g, ops, st);
         if (g.small_t < 0) {
             cudaError_t e = launch_grid<T, FORM, W, C, false, false, true>(g, ops, st);

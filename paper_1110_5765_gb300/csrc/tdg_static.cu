@@ -166,7 +166,7 @@ tdg_status run_static(bool nA, bool nB, long long M, long long N, long long K, l
     g.Rbar = nullptr;
     {
         const long long gam = (1LL << (bits - 1)) - 1;
-        g.small_t = small_t_ok(W, q_for((long long)L * gam * gam), (int)gam) ? 1 : 0;
+        g.small_t = small_round_ok(gform, W, q_for((long long)L * gam * gam), (int)gam) ? 1 : 0;
     }
     ST_TRY(launch_packed_gemm<T>(gform, W, g, ops, st));
     return TDG_OK;
