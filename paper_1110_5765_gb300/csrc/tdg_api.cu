@@ -727,7 +727,18 @@ extern "C" tdg_status tdgemm_gemm(tdgemm_plan_t p, void *C, double alpha, double
         a.L = p->L; a.nM = p->nM; a.nK = p->nK; a.nN = p->nN;
         a.pair = (const float *)p->pair; a.C = (float *)C; a.ldc = p->ldc;
         a.alpha = (float)alpha; a.beta = (float)beta; a.beta_zero = beta == 0.0;
-        cudaError_t e = launch_tc_gemm(fp8, a, ma, mb, st);
+        // C through TMA stores where it can be mapped (beta = 0 and 16-byte
+        // aligned rows), else through plain stores
+        CUtensorMap mc;
+        memset(&mc, 0, sizeof(mc));
+        a.c_tma = 0;
+        if (beta == 0.0 && ((uintptr_t)C & 15) == 0 && ((p->ldc * 4) & 15) == 0) {
+            int cbx, cby;
+            tc_gemm_c_box(&cbx, &cby);
+            a.c_tma = encode_map_2d(&mc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C, p->N, p->M, p->ldc,
+                                    cbx, cby, CU_TENSOR_MAP_SWIZZLE_64B) == CUDA_SUCCESS;
+        }
+        cudaError_t e = launch_tc_gemm(fp8, a, ma, mb, mc, st);
         if (e == cudaErrorNotSupported) return fail(TDG_EUNSUPPORTED, "tensor-core GEMM not built");
         CU_TRY(e);
         r = TDG_OK;

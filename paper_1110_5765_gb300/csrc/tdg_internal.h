@@ -198,9 +198,11 @@ struct TcArgs {
     long long ldc;
     float alpha, beta;
     int beta_zero;
+    int c_tma;            // 1: C written by TMA stores through mapC (beta = 0, C 16-byte aligned)
 };
 cudaError_t launch_tc_gemm(int fp8, const TcArgs &a, const CUtensorMap &mapA,
-                           const CUtensorMap &mapB, cudaStream_t st);
+                           const CUtensorMap &mapB, const CUtensorMap &mapC, cudaStream_t st);
+void tc_gemm_c_box(int *box_cols, int *box_rows);
 void tc_gemm_boxes(int fp8, int *box_rows_a, int *box_rows_b, int *box_k);
 
 }  // namespace tdg

@@ -20,9 +20,13 @@
 // own 128 rows x 256 columns of the accumulator.  Persistent clusters walk
 // their share of the tile pairs, the pipeline running on across tiles.
 //   warp 0      allocates 512 TMEM columns (both CTAs, collectively); lane 0
-//               streams 128-byte-wide k boxes of this CTA's A~ and B~ halves
-//               with 2-D TMA (128-byte swizzle) into a 5-deep ring, both
-//               CTAs' copies completing on the even CTA's mbarrier;
+//               streams 256 k-bytes of this CTA's A~ and B~ halves per stage
+//               (two 128-byte-wide boxes each, 2-D TMA with 128-byte
+//               swizzle) into a 3-deep ring, both CTAs' copies completing on
+//               the even CTA's mbarrier.  Eight MMAs per stage: the issuing
+//               thread's barrier operations between MMAs cost tensor-pipe
+//               time on GB300 (128 cycles per 256 x 256 x 16 MMA back to
+//               back, ~175-210 with a wait every four, ~152 every eight);
 //   warp 1      (even CTA) lane 0 issues the pair's tcgen05.mma into one of
 //               two TMEM accumulators, a fresh accumulation per slab, and
 //               commits to mbarriers in both CTAs that free ring stages and
@@ -48,16 +52,23 @@ namespace {
 
 constexpr int BM = 128, BN = 256;                  // per CTA: rows of A~, columns of C
 constexpr int BNH = BN / 2;                          // rows of B~ per CTA
-constexpr int STAGES = 5;                            // 4, 6 and 7 measured slower at 8192^3
-constexpr int ROW_BYTES = 128;                       // k-bytes per stage (one swizzle row)
-constexpr int STAGE_A = BM * ROW_BYTES;              // 16 KB
-constexpr int STAGE_B = BNH * ROW_BYTES;             // 16 KB
+constexpr int STAGES = 3;
+constexpr int ROW_BYTES = 128;                       // k-bytes per TMA box (one swizzle row)
+constexpr int BOXES = 2;                             // boxes per operand and stage
+constexpr int BOX_A = BM * ROW_BYTES;                // 16 KB
+constexpr int BOX_B = BNH * ROW_BYTES;               // 16 KB
+constexpr int STAGE_A = BOXES * BOX_A;               // 32 KB
+constexpr int STAGE_B = BOXES * BOX_B;               // 32 KB
+constexpr int MMAS_PER_BOX = 4;                      // 32 k-bytes per MMA
 constexpr uint32_t PAIR_TX = 2 * (STAGE_A + STAGE_B);   // bytes one stage brings into the pair
 constexpr int EPI_COLS = 64;                         // output columns per epilogue thread
 constexpr int EPI_WARPS = 4 * (BN / EPI_COLS);       // 4 TMEM lane quadrants x column groups
 constexpr int NUM_THREADS = 32 * (2 + EPI_WARPS);
 constexpr int TMEM_COLS = 512;                       // 2 accumulators x 256 fp32 columns
-constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * (STAGE_A + STAGE_B) + 256;
+// per epilogue warp: a 32-row x 16-column fp32 staging tile for the C store
+constexpr int STG_BYTES = 32 * 16 * 4;
+constexpr size_t SMEM_BYTES =
+    1024 /*alignment slack*/ + STAGES * (STAGE_A + STAGE_B) + EPI_WARPS * STG_BYTES + 256;
 
 // UMMA shared-memory descriptor, K-major operand with 128-byte swizzle:
 // 8-row x 128-byte atoms, 1024 bytes between 8-row groups.
@@ -112,6 +123,22 @@ __device__ inline void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint3
         " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
         "l"(map), "r"(bar_cl), "r"(x), "r"(y)
         : "memory");
+}
+
+// 2-D TMA store of a shared-memory box to global memory (out-of-range rows
+// and columns are not written), tracked in this thread's bulk group
+__device__ inline void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
+        "r"(smem_u32(src)), "r"(x), "r"(y)
+        : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ inline void tma_store_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ inline void tma_store_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // shared::cluster address of the variable at p's offset in CTA `rank`
@@ -175,21 +202,60 @@ __device__ inline bool tc_wait_epilogue(uint64_t *bar, uint32_t parity) {
     return mbar_wait_bounded_suspend(bar, parity, FP8 != 0);
 }
 
+// The plain-store path of the epilogue (beta != 0, or C rows that cannot be
+// mapped for TMA): 32 rows x 16 columns of C_acc from the warp's staging tile
+// (16-byte unit u of row r at u ^ ((r >> 1) & 3)), each store instruction
+// writing 8 rows x 64 contiguous bytes.  Kept out of line: inlined, its
+// address arithmetic made the promotion loop spill registers.
+__device__ __noinline__ void store_staged_plain(const TcArgs &g, const unsigned char *stg, int lane,
+                                                long long rbase, long long cbase, bool vec) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = 8 * i + (lane >> 2), u = lane & 3;
+        const float4 a4 = *reinterpret_cast<const float4 *>(stg + r * 64 + ((u ^ ((r >> 1) & 3)) * 16));
+        const long long grow = rbase + r;
+        const long long col = cbase + 4 * u;
+        if (grow >= g.M) continue;
+        float *crow = g.C + grow * g.ldc;
+        const float acc[4] = {a4.x, a4.y, a4.z, a4.w};
+        float o[4];
+        if (vec && col + 4 <= g.N) {
+            if (g.beta_zero) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o[q] = __fmul_rn(g.alpha, acc[q]);
+            } else {
+                const float4 in = *reinterpret_cast<const float4 *>(crow + col);
+                const float iv[4] = {in.x, in.y, in.z, in.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o[q] = __fmaf_rn(g.alpha, acc[q], __fmul_rn(g.beta, iv[q]));
+            }
+            *reinterpret_cast<float4 *>(crow + col) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (col + q < g.N)
+                    crow[col + q] = g.beta_zero ? __fmul_rn(g.alpha, acc[q])
+                                                : __fmaf_rn(g.alpha, acc[q], __fmul_rn(g.beta, crow[col + q]));
+        }
+    }
+}
+
 template <int FP8>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
-                   const __grid_constant__ CUtensorMap mapB, const TcArgs g) {
+                   const __grid_constant__ CUtensorMap mapB,
+                   const __grid_constant__ CUtensorMap mapC, const TcArgs g) {
     pdl_entry();
-    constexpr int BK = FP8 ? 128 : 64;          // k elements per stage
-    constexpr int KSTEP_BYTES = 32;             // one MMA: 16 fp16 or 32 e4m3 values
-    constexpr int MMAS_PER_STAGE = ROW_BYTES / KSTEP_BYTES;
+    constexpr int KB = FP8 ? 128 : 64;          // k elements per box (four MMAs of 32 bytes)
 
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled operand tiles
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = smem;
     unsigned char *sB = smem + STAGES * STAGE_A;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + STAGES * STAGE_B);
+    // C staging tiles (1024-byte aligned for the 64-byte swizzle of the C map), then barriers
+    unsigned char *stg_base = sB + STAGES * STAGE_B;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stg_base + EPI_WARPS * STG_BYTES);
     uint64_t *full = bars;                       // [STAGES]  TMA -> MMA
     uint64_t *empty = bars + STAGES;             // [STAGES]  MMA -> TMA
     uint64_t *acc_full = bars + 2 * STAGES;      // [2]       MMA -> epilogue
@@ -208,9 +274,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int tiles_n = (int)((g.N + BN - 1) / BN), tiles_m = (int)((g.M + BM - 1) / BM);
     const int npairs = tiles_n * ((tiles_m + 1) / 2);
     const int my_tiles = npairs > cid ? (npairs - 1 - cid) / ncl + 1 : 0;
-    const int slab_stages = g.L / BK;
+    // a slab is L / 16 (fp16) or L / 32 (E4M3) MMAs, a multiple of four (one
+    // box, since L % 64 == 0 or L % 128 == 0 respectively); a stage is two
+    // boxes, so slabs and stages share boundaries in boxes; a tile whose
+    // slabs span an odd number of boxes ends on a half-used stage (its
+    // second boxes read past the codes, which TMA fills with zeros)
     const int nslab = g.nK;
-    const int per_tile = nslab * slab_stages;
+    const int boxes_slab = g.L / KB;
+    const int per_tile = (nslab * boxes_slab + BOXES - 1) / BOXES;   // stages per tile
     const int total = my_tiles * per_tile;
     auto tile_origin = [&](int k, long long &m0, long long &n0) {
         const int t = cid + k * ncl;
@@ -260,17 +331,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     break;
                 }
                 if (*(volatile int *)abort_flag) break;
-                const int kt = it / per_tile, rem = it % per_tile;
-                const int l = rem / slab_stages, ks = rem % slab_stages;
-                const int kx = l * g.L + ks * BK;
+                const int kt = it / per_tile, j = it % per_tile;
+                const int kx = j * BOXES * KB;
                 long long m0, n0;
                 tile_origin(kt, m0, n0);
                 // this CTA's 128 rows of A~ and of B~; both CTAs' copies
                 // complete on the even CTA's full barrier, which expects them all
                 const uint32_t bar = cluster_addr(&full[stage], 0);
                 if (leader) mbar_arrive_expect_tx(&full[stage], PAIR_TX);
-                tma_load_2d_pair(sA + stage * STAGE_A, &mapA, bar, kx, (int)m0);
-                tma_load_2d_pair(sB + stage * STAGE_B, &mapB, bar, kx, (int)(n0 + rank * BNH));
+#pragma unroll
+                for (int x = 0; x < BOXES; ++x) {
+                    tma_load_2d_pair(sA + stage * STAGE_A + x * BOX_A, &mapA, bar, kx + x * KB, (int)m0);
+                    tma_load_2d_pair(sB + stage * STAGE_B + x * BOX_B, &mapB, bar, kx + x * KB,
+                                     (int)(n0 + rank * BNH));
+                }
             }
             // every copy issued must land before the CTA can exit: the pair's
             // MMA released each of the last stages only after reading them
@@ -280,34 +354,56 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0 && leader) {
-            int it = 0;
+            int it = 0;              // stages consumed
+            int stage = 0, box = 0;  // ring position; next box within the stage
+            uint32_t phase = 0;
+            uint64_t ad0 = 0, bd0 = 0;
             bool ok = true;
-            for (int gs = 0; gs < my_tiles * nslab && ok; ++gs) {   // global slab count
-                const int b = gs & 1;
-                if (gs >= 2 && !tc_wait<FP8>(&acc_empty[b], ((gs >> 1) + 1) & 1)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(b * BN);
-                for (int ks = 0; ks < slab_stages; ++ks, ++it) {
-                    const int stage = it % STAGES;
-                    if (!tc_wait<FP8>(&full[stage], (it / STAGES) & 1)) {
+            const int quads = boxes_slab;                 // 4-MMA groups per slab
+            for (int kt = 0; kt < my_tiles && ok; ++kt) {
+                for (int l = 0; l < nslab; ++l) {
+                    const int gs = kt * nslab + l;        // global slab count
+                    const int b = gs & 1;
+                    if (gs >= 2 && !tc_wait<FP8>(&acc_empty[b], ((gs >> 1) + 1) & 1)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t ad = desc_sw128(smem_u32(sA + stage * STAGE_A));
-                    const uint64_t bd = desc_sw128(smem_u32(sB + stage * STAGE_B));
+                    const uint32_t d = tmem + (uint32_t)(b * BN);
+                    for (int q = 0; q < quads; ++q) {
+                        if (box == 0) {
+                            if (!tc_wait<FP8>(&full[stage], phase)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            ad0 = desc_sw128(smem_u32(sA + stage * STAGE_A));
+                            bd0 = desc_sw128(smem_u32(sB + stage * STAGE_B));
+                        }
+                        const uint64_t ad = ad0 + (uint64_t)((box * BOX_A) >> 4);
+                        const uint64_t bd = bd0 + (uint64_t)((box * BOX_B) >> 4);
 #pragma unroll
-                    for (int kk = 0; kk < MMAS_PER_STAGE; ++kk) {
-                        const uint64_t adv = (uint64_t)((kk * KSTEP_BYTES) >> 4);
-                        mma2<FP8>(d, ad + adv, bd + adv, (ks | kk) != 0);
+                        for (int kk = 0; kk < MMAS_PER_BOX; ++kk) {
+                            const uint64_t adv = (uint64_t)((kk * 32) >> 4);
+                            mma2<FP8>(d, ad + adv, bd + adv, (q | kk) != 0);
+                        }
+                        if (++box == BOXES) {
+                            mma_commit_pair(&empty[stage]);     // frees the stage in both CTAs
+                            box = 0;
+                            ++it;
+                            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                        }
                     }
-                    mma_commit_pair(&empty[stage]);     // frees the stage in both CTAs
+                    if (!ok) break;
+                    mma_commit_pair(&acc_full[b]);          // the slab is complete in both TMEMs
                 }
-                if (!ok) break;
-                mma_commit_pair(&acc_full[b]);          // the slab is complete in both TMEMs
+                if (ok && box != 0) {
+                    // the tile ended inside a stage: release its unused half too
+                    mma_commit_pair(&empty[stage]);
+                    box = 0;
+                    ++it;
+                    if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                }
             }
             if (!ok) {
                 raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);
@@ -360,42 +456,69 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         __syncwarp();
                         if (lane == 0) mbar_arrive_cluster(acc_empty_cl[b]);
                     }
+                    // C_acc = fma(r, s_A s_B, C_acc) on column pairs: each lane
+                    // of fma.rn.f32x2 rounds once, as fmaf does
+                    uint64_t pr2;
+                    asm("mov.b64 %0, {%1, %1};" : "=l"(pr2) : "f"(pr));
 #pragma unroll
-                    for (int e = 0; e < 16; ++e)
-                        cacc[ch * 16 + e] = __fmaf_rn(v[e], pr, cacc[ch * 16 + e]);
-                }
-            }
-            if (!ok) break;
-            if (row < g.M) {
-                float *crow = g.C + row * g.ldc;
-                const bool vec = ((g.ldc & 3) == 0) && (((uintptr_t)g.C & 15) == 0);
-#pragma unroll
-                for (int c = 0; c < EPI_COLS; c += 4) {
-                    const long long col = col0 + c;
-                    float o[4];
-                    if (vec && col + 4 <= g.N) {
-                        if (g.beta_zero) {
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) o[q] = __fmul_rn(g.alpha, cacc[c + q]);
-                        } else {
-                            const float4 in = *reinterpret_cast<const float4 *>(crow + col);
-                            const float iv[4] = {in.x, in.y, in.z, in.w};
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                o[q] = __fmaf_rn(g.alpha, cacc[c + q], __fmul_rn(g.beta, iv[q]));
-                        }
-                        *reinterpret_cast<float4 *>(crow + col) = make_float4(o[0], o[1], o[2], o[3]);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (col + q < g.N)
-                                crow[col + q] = g.beta_zero
-                                                    ? __fmul_rn(g.alpha, cacc[c + q])
-                                                    : __fmaf_rn(g.alpha, cacc[c + q], __fmul_rn(g.beta, crow[col + q]));
+                    for (int e = 0; e < 16; e += 2) {
+                        uint64_t v2, c2;
+                        asm("mov.b64 %0, {%1, %2};" : "=l"(v2) : "f"(v[e]), "f"(v[e + 1]));
+                        asm("mov.b64 %0, {%1, %2};" : "=l"(c2) : "f"(cacc[ch * 16 + e]), "f"(cacc[ch * 16 + e + 1]));
+                        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c2) : "l"(v2), "l"(pr2));
+                        asm("mov.b64 {%0, %1}, %2;" : "=f"(cacc[ch * 16 + e]), "=f"(cacc[ch * 16 + e + 1]) : "l"(c2));
                     }
                 }
             }
+            if (!ok) break;
+            // C out through this warp's staging tile, 16 columns at a time: the
+            // thread of row r writes its 16 values as row r (16-byte units
+            // XOR-swizzled by row, conflict-free), then each store instruction
+            // of the warp writes 8 rows x 64 contiguous bytes (a thread per
+            // 16 bytes) instead of 32 rows x 16 bytes
+            unsigned char *stg = stg_base + ew * STG_BYTES;
+            const bool vec = ((g.ldc & 3) == 0) && (((uintptr_t)g.C & 15) == 0);
+            const long long rbase = m0 + quad * 32;
+            if (g.c_tma) {
+                // beta = 0: alpha C_acc staged in the C map's 64-byte swizzle
+                // (16-byte unit u of row r at u ^ ((r >> 1) & 3)), written by
+                // one TMA store per 32 x 16 box, which clips rows and columns
+                // outside C
+#pragma unroll
+                for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
+                    if (ch > 0 && lane == 0) tma_store_wait_read();   // the box before is read
+                    __syncwarp();
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int us = u ^ ((lane >> 1) & 3);
+                        const float *cu = cacc + ch * 16 + 4 * u;
+                        *reinterpret_cast<float4 *>(stg + lane * 64 + us * 16) =
+                            make_float4(__fmul_rn(g.alpha, cu[0]), __fmul_rn(g.alpha, cu[1]),
+                                        __fmul_rn(g.alpha, cu[2]), __fmul_rn(g.alpha, cu[3]));
+                    }
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) tma_store_2d(&mapC, stg, (int)(col0 + ch * 16), (int)rbase);
+                }
+                if (lane == 0) tma_store_wait_read();
+                __syncwarp();
+                continue;
+            }
+#pragma unroll
+            for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int us = u ^ ((lane >> 1) & 3);
+                    *reinterpret_cast<float4 *>(stg + lane * 64 + us * 16) =
+                        make_float4(cacc[ch * 16 + 4 * u], cacc[ch * 16 + 4 * u + 1],
+                                    cacc[ch * 16 + 4 * u + 2], cacc[ch * 16 + 4 * u + 3]);
+                }
+                __syncwarp();
+                store_staged_plain(g, stg, lane, rbase, col0 + ch * 16, vec);
+                __syncwarp();
+            }
         }
+        if (lane == 0) tma_store_wait_all();
         if (!ok) {
             raise_status(const_cast<DevPlan *>(g.plan), TDG_ETIMEOUT);
             *abort_flag = 1;
@@ -417,7 +540,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 template <int FP8>
 static cudaError_t launch_tc(const TcArgs &a, const CUtensorMap &mapA, const CUtensorMap &mapB,
-                             cudaStream_t st) {
+                             const CUtensorMap &mapC, cudaStream_t st) {
     auto kern = tc_gemm_kernel<FP8>;
     static int max_clusters = 0;
     cudaLaunchConfig_t cfg = {};
@@ -451,18 +574,23 @@ static cudaError_t launch_tc(const TcArgs &a, const CUtensorMap &mapA, const CUt
     // the launch: cluster shape, and programmatic serialisation unless the grid
     // leaves SMs idle
     cfg.numAttrs = pdl_for_grid(cfg.gridDim.x) ? 2 : 1;
-    return cudaLaunchKernelEx(&cfg, kern, mapA, mapB, a);
+    return cudaLaunchKernelEx(&cfg, kern, mapA, mapB, mapC, a);
 }
 
 cudaError_t launch_tc_gemm(int fp8, const TcArgs &a, const CUtensorMap &mapA,
-                           const CUtensorMap &mapB, cudaStream_t st) {
-    return fp8 ? launch_tc<1>(a, mapA, mapB, st) : launch_tc<0>(a, mapA, mapB, st);
+                           const CUtensorMap &mapB, const CUtensorMap &mapC, cudaStream_t st) {
+    return fp8 ? launch_tc<1>(a, mapA, mapB, mapC, st) : launch_tc<0>(a, mapA, mapB, mapC, st);
+}
+
+void tc_gemm_c_box(int *box_cols, int *box_rows) {
+    *box_cols = 16;            // one epilogue warp's staging tile
+    *box_rows = 32;
 }
 
 void tc_gemm_boxes(int fp8, int *box_rows_a, int *box_rows_b, int *box_k) {
     *box_rows_a = BM;
     *box_rows_b = BNH;         // each CTA of a pair loads half of the B~ tile
-    *box_k = fp8 ? 128 : 64;
+    *box_k = fp8 ? 128 : 64;   // two boxes per operand and stage
 }
 
 }  // namespace tdg

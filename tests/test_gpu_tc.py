@@ -191,3 +191,68 @@ def test_tc_fp8_precision_size_sampled(tdg, orc):
     sg = orc.snr_db(np.concatenate([x.ravel() for x in got]), ex)
     so = orc.snr_db(np.concatenate([x.ravel() for x in want]), ex)
     assert abs(sg - so) < 0.1, (sg, so)
+
+
+def _fma32(a, b, c):
+    """fp32 fma(a, b, c) with one rounding, elementwise (exact rationals)."""
+    from fractions import Fraction
+    a, b, c = (np.asarray(x, np.float32) for x in (a, b, c))
+    out = np.empty(a.shape, np.float32)
+    fa, fb, fc = a.ravel(), b.ravel(), c.ravel()
+    o = out.ravel()
+    for i in range(fa.size):
+        v = Fraction(float(fa[i])) * Fraction(float(fb[i])) + Fraction(float(fc[i]))
+        o[i] = np.float32(float(v)) if v == 0 else _round32(v)
+    return out
+
+
+def _round32(v):
+    """Round a rational to the nearest fp32, ties to even (no overflow here)."""
+    from fractions import Fraction
+    import math
+    sign = -1 if v < 0 else 1
+    v = abs(v)
+    e = math.floor(math.log2(v.numerator) - math.log2(v.denominator))
+    while Fraction(2) ** e > v:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= v:
+        e += 1
+    q = max(e, -126) - 23                      # quantum of the binade (subnormals below 2^-126)
+    m = v / Fraction(2) ** q
+    n = m.numerator // m.denominator
+    r = m - n
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    return np.float32(sign * float(Fraction(n) * Fraction(2) ** q))
+
+
+@pytest.mark.parametrize("L", [64, 128])
+def test_tc_int_output_paths_alpha_beta_ldc(tdg, orc, L):
+    """The three ways C leaves the tensor-core kernel: TMA stores (beta = 0,
+    16-byte aligned rows), plain stores with beta != 0 (C read back), and
+    plain stores where a row pitch of N + 1 floats rules the TMA map out.
+    Each equals alpha * C_oracle (one fp32 rounding) or fma(alpha, C_oracle,
+    beta * C_in) bit for bit; 300 rows and 260 columns leave ragged edge tiles."""
+    M, K, N = 300, 256, 260
+    A = synth.laplace((M, K), 71, np.float32)
+    B = synth.laplace((K, N), 72, np.float32)
+    ref = orc.tc_int_gemm(A, B, L=L, bits=8).C.astype(np.float32)
+    alpha = np.float32(0.75)
+    cases = [(0.0, N), (-1.5, N), (0.0, N + 1)]
+    for beta, ldc in cases:
+        p = tdg.Plan(M, N, K, L=L, W=1, dtype="f32", form="tc_int", bits=8, ldc=ldc)
+        Cin = synth.gaussian((M, ldc), 73, np.float32)
+        Cfull = dev(Cin)
+        C = Cfull[:, :N]
+        p.run(dev(A), dev(B), C, float(alpha), beta)
+        torch.cuda.synchronize()
+        assert p.info()["device_status"] == 0
+        p.close()
+        got = Cfull.cpu().numpy()
+        if beta == 0.0:
+            want = (alpha * ref).astype(np.float32)
+        else:
+            want = _fma32(np.full_like(ref, alpha), ref, (np.float32(beta) * Cin[:, :N]).astype(np.float32))
+        assert same_bits(got[:, :N], want), (beta, ldc)
+        if ldc > N:
+            assert same_bits(got[:, N:], Cin[:, N:]), "padding column written"
