@@ -489,7 +489,7 @@ __device__ inline void df_add_sq(float &hi, float &lo, float x) {
     lo = __fadd_rn(lo, __fadd_rn(err, e));
 }
 
-constexpr int kFusedThreads = 256;
+constexpr int kFusedThreads = 512;   // 32 values per thread at L = 128 (two CTAs, 32 warps per SM)
 
 // block statistics of the values this thread holds, reduced over the CTA;
 // thread 0 writes them with the compander, every thread returns c
@@ -550,12 +550,12 @@ __device__ inline float fused_block_companders(const float (&v)[NVAL], const Fus
 }
 
 template <int FP8, int L>
-__global__ void __launch_bounds__(kFusedThreads)
+__global__ void __launch_bounds__(kFusedThreads, 2)
     codes_stats_kernel(FusedOp A, FusedOp B, long long nblkA, double gamma, long long ldo,
                        DevPlan *plan) {
     pdl_entry();
     constexpr int ES = FP8 ? 1 : 2;
-    constexpr int NV = L * L / kFusedThreads;    // values per thread: 64 at L = 128
+    constexpr int NV = L * L / kFusedThreads;    // values per thread: 32 at L = 128
     extern __shared__ float s_tile[];            // x-contiguous inputs: s[k][x], pitch L + 1
     const bool isA = (long long)blockIdx.x < nblkA;
     const FusedOp &o = isA ? A : B;
