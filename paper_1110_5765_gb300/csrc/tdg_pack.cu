@@ -625,17 +625,40 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
             for (int i = 0; i < 4; ++i) s_tile[kr * P + xr + i] = v[4 * u + i];
         }
         __syncthreads();
-        // items: 8 consecutive k of one row x, lanes along x (conflict-free reads)
+        // items: 8 consecutive k of one row x, lanes along x (conflict-free
+        // reads), encoded into the code tile cs[x][k] (row pitch CP bytes:
+        // the lanes' 8- or 16-byte writes fall in distinct banks) ...
+        constexpr int CP = FP8 ? L + 8 : 2 * L + 16;
+        unsigned char *cs = reinterpret_cast<unsigned char *>(s_tile + L * P);
         for (int e = threadIdx.x; e < L * L / 8; e += kFusedThreads) {
             const int xr = e % L, kr = (e / L) * 8;
-            const long long k = k0 + kr;
-            if (xr >= xn || k >= ldo) continue;
             float w[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) w[i] = __fmul_rn(s_tile[(kr + i) * P + xr], c);
-            encode8<FP8>(w, o.out + ((x0 + xr) * ldo + k) * ES);
+            encode8<FP8>(w, cs + xr * CP + kr * ES);
+        }
+        __syncthreads();
+        // ... and copied out row by row: consecutive lanes write consecutive
+        // 8 bytes (E4M3) or 16 bytes (fp16) of one row of codes
+        constexpr int UB = FP8 ? 8 : 16;             // bytes per unit
+        constexpr int UPR = L * ES / UB;             // units per row of the tile
+        for (int e = threadIdx.x; e < L * UPR; e += kFusedThreads) {
+            const int xr = e / UPR, u = e % UPR;
+            const long long k = k0 + (long long)u * (UB / ES);
+            if (xr >= xn || k >= ldo) continue;
+            unsigned char *dst = o.out + ((x0 + xr) * ldo + k) * ES;
+            if constexpr (FP8)
+                *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(cs + xr * CP + u * UB);
+            else
+                *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(cs + xr * CP + u * UB);
         }
     }
+}
+
+// dynamic shared memory of codes_stats_kernel for x-contiguous inputs: the
+// fp32 tile s[k][x] (pitch L + 1) and the code tile (pitch L + 8 or 2 L + 16 bytes)
+constexpr size_t fused_xc_smem(int fp8, int L) {
+    return (size_t)L * (L + 1) * sizeof(float) + (size_t)L * (fp8 ? L + 8 : 2 * L + 16);
 }
 
 template <typename T>
@@ -793,16 +816,17 @@ cudaError_t launch_codes_stats(const PackOperand<float> &a, double *mxA, double 
     const long long na = fa.nbx * fa.nbk, nb = b ? fb.nbx * fb.nbk : 0;
     if (na + nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const bool xc = a.sk != 1 || (b && b->sk != 1);
-    const size_t smem = xc ? (size_t)L * (L + 1) * sizeof(float) : 0;
+    const size_t smem = xc ? fused_xc_smem(fp8, L) : 0;
     auto kern = L == 128 ? (fp8 ? codes_stats_kernel<1, 128> : codes_stats_kernel<0, 128>)
                          : (fp8 ? codes_stats_kernel<1, 64> : codes_stats_kernel<0, 64>);
     static std::once_flag attr_once;
     cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [&]() {
-        // the L = 128 tile needs 66 KB of dynamic shared memory
-        for (auto k : {codes_stats_kernel<0, 128>, codes_stats_kernel<1, 128>}) {
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(128 * 129 * sizeof(float)));
+        // the L = 128 tiles need 82-99 KB of dynamic shared memory
+        for (int f8 = 0; f8 < 2; ++f8) {
+            cudaError_t e = cudaFuncSetAttribute(f8 ? codes_stats_kernel<1, 128> : codes_stats_kernel<0, 128>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)fused_xc_smem(f8, 128));
             if (e != cudaSuccess) attr_err = e;
         }
     });
