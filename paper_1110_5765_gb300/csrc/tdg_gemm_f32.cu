@@ -15,7 +15,11 @@ cudaError_t launch_packed_gemm<float>(int form, int W, const GemmArgs<float> &g,
     using S = TilesF32;
     using A = TilesF32Asym;
     using A2 = TilesF32AsymW2;
-    if (form == G_PLAIN) return go<G_PLAIN, 1, S>(g, ops, st);
+    if (form == G_PLAIN) {
+        const long long tiles = ((g.Mrows + S::BM - 1) / S::BM) * ((g.N + S::BN - 1) / S::BN);
+        if (2 * tiles <= device_sms()) return go<G_PLAIN, 1, TilesF32Small>(g, ops, st);
+        return go<G_PLAIN, 1, S>(g, ops, st);
+    }
     if (form == G_SYM) {
         switch (W) {
             case 1: return go<G_SYM, 1, S>(g, ops, st);

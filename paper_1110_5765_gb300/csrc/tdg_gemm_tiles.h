@@ -14,6 +14,11 @@ struct Tiles {
 // (the best of a sweep of k-tile, ring depth and thread tile on GB300 with the
 // packed f32x2 main loop; 96 KB of ring keeps two CTAs per SM)
 using TilesF32 = Tiles<128, 128, 8, 8, 32, 3>;
+// fp32 plain product with few output tiles (at most half as many 128 x 128 tiles
+// as SMs, e.g. 288 x 288 x 21600): 64 x 64 tiles, 4 x 4 per thread, so that four
+// times as many SMs share the work (the conventional product does not split k,
+// which would change its summation order)
+using TilesF32Small = Tiles<64, 64, 4, 4, 32, 4>;
 // fp32 asymmetric: 64 packed rows (W result rows each) x 128 columns
 using TilesF32Asym = Tiles<64, 128, 4, 8, 16, 6>;     // W >= 3: W x 32 running sums per thread
 using TilesF32AsymW2 = Tiles<128, 128, 8, 8, 32, 3>;  // W <= 2: W x 64 sums fit TMEM, 2.6 % faster

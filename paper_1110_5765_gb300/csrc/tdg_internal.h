@@ -40,7 +40,7 @@ cudaError_t launch_block_stats(const T *A, long long rows_a, long long cols_a, l
 // choice of W / z / companders into *plan, then c, s per block and the
 // de-companding factors.
 // scales_done: c and s per block were already written (the fused tensor-core
-// path): the de-companding factors are formed from them.
+// path), so the compander kernel is not launched.
 template <typename T>
 cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double *eA,
                            const double *mB, const double *eB, const double *stab,

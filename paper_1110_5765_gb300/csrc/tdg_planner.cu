@@ -324,58 +324,42 @@ __global__ void __launch_bounds__(32) planner_kernel(PlanParams pp, const double
     decide_plan(pp, agg, stab, res, plan);
 }
 
-// Companders and de-companding factors, one CTA per (slab l, band of up to
-// kPairRows block rows): c = gamma / max|x| (fp64, rounded to T for eq. 3) and
-// s = 1/c for the band's A blocks (i, l) and for every B block (l, j) (the
-// band-0 CTA writes B's), then (T)(s_A,il * s_B,lj) for the band's (i, j) in
-// layout [l][i][j].  No CTA reads what another writes.
-constexpr int kPairRows = 64;
-constexpr int kPairThreads = 256;
-
+// c = gamma / max|x| (fp64, rounded to T for eq. 3), s = 1/c, per block.
 template <typename T>
-__global__ void __launch_bounds__(kPairThreads)
-    scales_pairs_kernel(PlanParams pp, const double *__restrict__ mA, const double *__restrict__ mB,
-                        const DevPlan *__restrict__ plan, T *cA, double *sA, T *cB, double *sB,
-                        T *pair, int scales_done) {
+__global__ void scales_kernel(PlanParams pp, const double *__restrict__ mA,
+                              const double *__restrict__ mB, const DevPlan *__restrict__ plan,
+                              T *cA, double *sA, T *cB, double *sB) {
     pdl_entry();
+    const long long nAblk = (long long)pp.nM * pp.nK, nBblk = (long long)pp.nK * pp.nN;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const DevPlan a = *plan;
     if (!needs_companders(pp, a)) return;  // plain product: nothing to compand
-    __shared__ double s_rows[kPairRows];
-    const int l = (int)blockIdx.x;
-    const long long i0 = (long long)blockIdx.y * kPairRows;
-    const int ni = (int)min((long long)kPairRows, (long long)pp.nM - i0);
-    auto scale = [&](double m, bool isA) {
+    for (long long k = idx; k < nAblk + nBblk; k += (long long)gridDim.x * blockDim.x) {
+        const bool isA = k < nAblk;
+        const long long b = isA ? k : k - nAblk;
+        double m = isA ? mA[b] : mB[b];
         double c;
         if (pp.mode == MODE_MANUAL) c = isA ? pp.manual_cA : pp.manual_cB;
         else c = m > 0.0 ? __ddiv_rn((double)(isA ? a.gA : a.gB), m) : 0.0;
-        return c;
-    };
-    for (int t = threadIdx.x; t < ni; t += blockDim.x) {
-        const long long b = (i0 + t) * pp.nK + l;
-        double s;
-        if (scales_done) {
-            s = sA[b];
-        } else {
-            const double c = scale(mA[b], true);
-            s = c > 0.0 ? __ddiv_rn(1.0, c) : 0.0;
-            cA[b] = (T)c;
-            sA[b] = s;
-        }
-        s_rows[t] = s;
+        double s = c > 0.0 ? __ddiv_rn(1.0, c) : 0.0;
+        if (isA) { cA[b] = (T)c; sA[b] = s; }
+        else { cB[b] = (T)c; sB[b] = s; }
     }
-    __syncthreads();
-    for (long long j = threadIdx.x; j < pp.nN; j += blockDim.x) {
-        const long long b = (long long)l * pp.nN + j;
-        double s;
-        if (scales_done) {
-            s = sB[b];
-        } else {
-            const double c = scale(mB[b], false);
-            s = c > 0.0 ? __ddiv_rn(1.0, c) : 0.0;
-            if (blockIdx.y == 0) { cB[b] = (T)c; sB[b] = s; }
-        }
-        T *row = pair + ((long long)l * pp.nM + i0) * pp.nN + j;
-        for (int t = 0; t < ni; ++t) row[(long long)t * pp.nN] = (T)__dmul_rn(s_rows[t], s);
+}
+
+// (T)(s_A,il * s_B,lj) for every (l, i, j), layout [l][i][j]
+template <typename T>
+__global__ void pairs_kernel(PlanParams pp, const double *__restrict__ sA,
+                             const double *__restrict__ sB, const DevPlan *__restrict__ plan,
+                             T *pair) {
+    pdl_entry();
+    if (!needs_companders(pp, *plan)) return;
+    const long long n = (long long)pp.nK * pp.nM * pp.nN;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        long long j = k % pp.nN, r = k / pp.nN;
+        long long i = r % pp.nM, l = r / pp.nM;
+        pair[k] = (T)__dmul_rn(sA[i * pp.nK + l], sB[l * pp.nN + j]);
     }
 }
 
@@ -572,11 +556,17 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
                        (const LevelRec *)res, plan);
     }
     if (e != cudaSuccess) return e;
-    if (pp.nM < 1 || pp.nK < 1 || pp.nK > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    const dim3 grid((unsigned)pp.nK, (unsigned)((pp.nM + kPairRows - 1) / kPairRows));
-    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    return launch_pdl(scales_pairs_kernel<T>, grid, dim3(kPairThreads), 0, st, pp, mA, mB,
-                      (const DevPlan *)plan, cA, sA, cB, sB, pair, scales_done ? 1 : 0);
+    if (!scales_done) {
+        long long nblk = (long long)pp.nM * pp.nK + (long long)pp.nK * pp.nN;
+        int g = (int)min((nblk + 255) / 256, 4096LL);
+        e = launch_pdl(scales_kernel<T>, dim3(g), dim3(256), 0, st, pp, mA, mB,
+                       (const DevPlan *)plan, cA, sA, cB, sB);
+        if (e != cudaSuccess) return e;
+    }
+    long long np = (long long)pp.nK * pp.nM * pp.nN;
+    int g = (int)min((np + 255) / 256, 8192LL);
+    return launch_pdl(pairs_kernel<T>, dim3(g), dim3(256), 0, st, pp, (const double *)sA,
+                      (const double *)sB, (const DevPlan *)plan, pair);
 }
 
 template cudaError_t launch_planner<float>(const PlanParams &, const double *, const double *,
