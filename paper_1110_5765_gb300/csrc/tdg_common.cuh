@@ -34,6 +34,10 @@ struct DevPlan {
     double s_rep;      // representation-noise RMSE the model used (0 if none)
     double S, T1, T2, T3;  // noise-model aggregates
     unsigned int levels_done;  // candidate-level CTAs finished (the last one decides)
+    // planner inputs, written by the last per-slab aggregate CTA before the
+    // decision: the slab sums S, T1, T2, T3 (unscaled) and rho = sqrt(T2 / T1)
+    unsigned int aggs_done;
+    double tS, tT1, tT2, tT3, trho;
 };
 
 // Per-slab aggregates X_l = sum_i sigma_A,il^2, MA_l = sum_i m_A,il^2,

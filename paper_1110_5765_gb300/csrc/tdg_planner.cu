@@ -57,20 +57,6 @@ __device__ inline double snr_db(double S, double N) {
     return N <= 0.0 ? INFINITY : 10.0 * log10(S / N);
 }
 
-// Per-slab aggregates (slab_aggregate_warp): one warp per slab on its own SM
-// (GB300's fp64 rate is a small fraction of fp32, so the sums are spread over
-// the GPU rather than serialised on one SM).
-__global__ void __launch_bounds__(32) slab_aggregates_kernel(PlanParams pp,
-                                                             const double *__restrict__ mA,
-                                                             const double *__restrict__ vA,
-                                                             const double *__restrict__ mB,
-                                                             const double *__restrict__ vB,
-                                                             double *__restrict__ agg) {
-    pdl_entry();
-    if (pp.mode == MODE_MANUAL) return;
-    slab_aggregate_warp((int)blockIdx.x, pp.nM, pp.nK, pp.nN, mA, vA, mB, vB, agg);
-}
-
 // S / L, T1, T2, T3: products of the per-slab aggregates summed over slabs by
 // one warp (lanes over l, then a fixed xor tree); every caller gets the same
 // bits.
@@ -80,8 +66,8 @@ __device__ inline void slab_totals(const PlanParams &pp, const double *__restric
     S = T1 = T2 = T3 = 0.0;
     if (pp.mode != MODE_MANUAL) {
         for (int l = lane; l < pp.nK; l += 32) {
-            const double X = agg[4 * (long long)l], MA = agg[4 * (long long)l + 1];
-            const double Y = agg[4 * (long long)l + 2], MB = agg[4 * (long long)l + 3];
+            const double X = __ldcg(&agg[4 * (long long)l]), MA = __ldcg(&agg[4 * (long long)l + 1]);
+            const double Y = __ldcg(&agg[4 * (long long)l + 2]), MB = __ldcg(&agg[4 * (long long)l + 3]);
             S += X * Y;
             T1 += X * MB;
             T2 += Y * MA;
@@ -99,6 +85,56 @@ __device__ inline void slab_totals(const PlanParams &pp, const double *__restric
 
 __device__ inline double rho_of(double T1, double T2) {
     return (T1 <= 0.0 || T2 <= 0.0) ? 1.0 : sqrt(T2 / T1);
+}
+
+// Per-slab aggregates (slab_aggregate_warp): one warp per slab on its own SM
+// (GB300's fp64 rate is a small fraction of fp32, so the sums are spread over
+// the GPU rather than serialised on one SM).  The last warp to finish (a
+// counter in the plan record, no waiting) sums the slabs and forms rho once,
+// for every candidate and the decision to read.
+__global__ void __launch_bounds__(32) slab_aggregates_kernel(PlanParams pp,
+                                                             const double *__restrict__ mA,
+                                                             const double *__restrict__ vA,
+                                                             const double *__restrict__ mB,
+                                                             const double *__restrict__ vB,
+                                                             double *__restrict__ agg,
+                                                             DevPlan *plan) {
+    pdl_entry();
+    if (pp.mode == MODE_MANUAL) return;
+    slab_aggregate_warp((int)blockIdx.x, pp.nM, pp.nK, pp.nN, mA, vA, mB, vB, agg);
+    unsigned int prev = 0;
+    if ((threadIdx.x & 31) == 0) {      // the lane that wrote this slab's aggregates
+        __threadfence();
+        prev = atomicAdd(&plan->aggs_done, 1u);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev + 1 != gridDim.x) return;
+    __threadfence();
+    double S, T1, T2, T3;
+    slab_totals(pp, agg, S, T1, T2, T3);
+    if ((threadIdx.x & 31) == 0) {
+        plan->tS = S;
+        plan->tT1 = T1;
+        plan->tT2 = T2;
+        plan->tT3 = T3;
+        plan->trho = rho_of(T1, T2);
+    }
+}
+
+// The slab sums and rho the last aggregate CTA wrote (zero for manual plans,
+// which launch no aggregates)
+__device__ inline void load_totals(const PlanParams &pp, const DevPlan *plan, double &S, double &T1,
+                                   double &T2, double &T3, double &rho) {
+    if (pp.mode == MODE_MANUAL) {
+        S = T1 = T2 = T3 = 0.0;
+        rho = rho_of(0.0, 0.0);
+        return;
+    }
+    S = __ldcg(&plan->tS);
+    T1 = __ldcg(&plan->tT1);
+    T2 = __ldcg(&plan->tT2);
+    T3 = __ldcg(&plan->tT3);
+    rho = __ldcg(&plan->trho);
 }
 
 // Target mode, packed forms: every candidate (W, R_max level t) evaluated in
@@ -137,14 +173,13 @@ __device__ void decide_plan(const PlanParams &pp, const double *__restrict__ agg
                             const double *__restrict__ stab, const LevelRec *res, DevPlan *plan) {
     const int lane = threadIdx.x & 31;
     const int L = pp.L;
-    double S, T1, T2, T3;
-    slab_totals(pp, agg, S, T1, T2, T3);
+    double S, T1, T2, T3, rho;
+    load_totals(pp, plan, S, T1, T2, T3, rho);
     DevPlan a{};
     a.S = (double)L * S;
     a.T1 = T1;
     a.T2 = T2;
     a.T3 = T3;
-    const double rho = rho_of(a.T1, a.T2);
     a.status = 0;
     a.level = -1;
     a.pred_snr = NAN;
@@ -279,12 +314,11 @@ __global__ void __launch_bounds__(32) level_kernel(PlanParams pp, const double *
     const int per_w = (nlev + 31) / 32;                 // CTAs per W
     const int W = pp.Wreq - (int)blockIdx.x / per_w;
     const int t = t_lo + ((int)blockIdx.x % per_w) * 32 + lane;
-    double S, T1, T2, T3;
-    slab_totals(pp, agg, S, T1, T2, T3);
+    double S, T1, T2, T3, rho;
+    load_totals(pp, plan, S, T1, T2, T3, rho);
     if (W >= 2 && t <= t_hi) {
         DevPlan a{};
         a.S = (double)L * S; a.T1 = T1; a.T2 = T2; a.T3 = T3;
-        const double rho = rho_of(T1, T2);
         LevelRec r{};
         r.n = -1.0;
         const long long Rt = r_level(t);
@@ -538,8 +572,8 @@ cudaError_t launch_planner(const PlanParams &pp, const double *mA, const double 
     // agg: 4 nK per-slab aggregates, then one record per candidate (W, level)
     LevelRec *res = reinterpret_cast<LevelRec *>(agg + 4 * (long long)pp.nK);
     if (pp.mode != MODE_MANUAL) {
-        cudaError_t e0 =
-            launch_pdl(slab_aggregates_kernel, dim3(pp.nK), dim3(32), 0, st, pp, mA, eA, mB, eB, agg);
+        cudaError_t e0 = launch_pdl(slab_aggregates_kernel, dim3(pp.nK), dim3(32), 0, st, pp, mA, eA,
+                                    mB, eB, agg, plan);
         if (e0 != cudaSuccess) return e0;
     }
     cudaError_t e;
