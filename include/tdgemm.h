@@ -26,7 +26,8 @@
  *     cudaStream_t (NULL = the legacy default stream).
  *   - The plan owns every other device buffer (statistics, companders, packed
  *     operands) and frees it in tdgemm_plan_destroy.
- *   - All device work is queued on `stream`; no entry point synchronises the
+ *   - All device work is queued on `stream` (tdgemm_run_host_async also
+ *     uses a copy stream of the plan's); no entry point synchronises the
  *     host except tdgemm_plan_info, tdgemm_unpack (when given host buffers)
  *     and tdgemm_run_host.
  *   - Argument errors are returned at once and leave the plan unchanged.
@@ -260,6 +261,22 @@ tdg_status tdgemm_run(tdgemm_plan_t plan, const void *A, const void *B, void *C,
  */
 tdg_status tdgemm_run_host(tdgemm_plan_t plan, const void *A, const void *B, void *C,
                            double alpha, double beta, void *stream);
+
+/*
+ * The same, pipelined for a sequence of products with HOST buffers: queues
+ * the copies of A and B (and of C when beta != 0) on a copy stream the plan
+ * owns, into the first of two device staging sets that the computation
+ * queued earlier no longer reads, then the computation on `stream` after
+ * them, and the copy of C back (unless C is written in place, as above); it
+ * returns without synchronising.  The copies of one call therefore run while
+ * the computation of the previous call does.  A, B and C must be pinned host
+ * memory (page-locked, cudaHostAlloc / cudaHostRegister: TDG_EINVAL
+ * otherwise) and must stay unchanged (A, B) and unread (C) until `stream`
+ * has finished the call's work; successive calls on one plan must use the
+ * same `stream`.  Results are bit-identical to tdgemm_run_host's.
+ */
+tdg_status tdgemm_run_host_async(tdgemm_plan_t plan, const void *A, const void *B, void *C,
+                                 double alpha, double beta, void *stream);
 
 /*
  * Unfused step (d) for checking the integer domain: needs TDG_KEEP_PACKED and

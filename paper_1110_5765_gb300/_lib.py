@@ -27,7 +27,8 @@ STATUS = {0: "TDG_OK", 1: "TDG_EINVAL", 2: "TDG_ENOMEM", 3: "TDG_ECUDA", 4: "TDG
 EXPORTS = ["tdgemm_plan", "tdgemm_set_rep_noise", "tdgemm_set_manual",
            "tdgemm_set_kernel_control", "tdgemm_kernel_mask", "tdgemm_quantize_pack",
            "tdgemm_quantize_pack_a",
-           "tdgemm_gemm", "tdgemm_run", "tdgemm_run_host", "tdgemm_unpack", "tdgemm_plan_info",
+           "tdgemm_gemm", "tdgemm_run", "tdgemm_run_host", "tdgemm_run_host_async", "tdgemm_unpack",
+           "tdgemm_plan_info",
            "tdgemm_plan_destroy", "tdgemm_snr", "tdgemm_run_static", "tdgemm_set_wait_test",
            "tdgemm_set_speedup",
            "tdgemm_fma_probe", "tdgemm_last_error", "tdgemm_version"]
@@ -70,6 +71,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.tdgemm_gemm.argtypes = [vp, vp, dbl, dbl, vp]
     L.tdgemm_run.argtypes = [vp, vp, vp, vp, dbl, dbl, vp]
     L.tdgemm_run_host.argtypes = [vp, vp, vp, vp, dbl, dbl, vp]
+    L.tdgemm_run_host_async.argtypes = [vp, vp, vp, vp, dbl, dbl, vp]
     L.tdgemm_unpack.argtypes = [vp, vp, vp, vp]
     L.tdgemm_plan_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.tdgemm_plan_destroy.argtypes = [vp]

@@ -220,6 +220,19 @@ class Plan:
                                       float(alpha), float(beta), _stream_ptr(stream)))
         return C
 
+    def run_host_async(self, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor,
+                       alpha: float = 1.0, beta: float = 0.0, stream=None) -> torch.Tensor:
+        """Pinned host tensors; queues the copies on the plan's copy stream and the
+        computation on `stream`, without synchronising: the copies of one call
+        overlap the computation of the previous one.  C is final (and A, B may
+        be reused) once `stream` has finished."""
+        for X in (A, B, C):
+            if X.is_cuda or not X.is_contiguous() or not X.is_pinned():
+                raise ValueError("run_host_async takes contiguous pinned host tensors")
+        check(self._L.tdgemm_run_host_async(self._h, A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                                            float(alpha), float(beta), _stream_ptr(stream)))
+        return C
+
     def unpack(self, rint_out: torch.Tensor | None = None, C: torch.Tensor | None = None,
                stream=None):
         check(self._L.tdgemm_unpack(self._h, rint_out.data_ptr() if rint_out is not None else None,

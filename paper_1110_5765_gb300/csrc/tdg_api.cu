@@ -99,6 +99,16 @@ struct tdgemm_plan_s {
     bool have_table = false;
     // host-buffer staging (tdgemm_run_host)
     void *hA = nullptr, *hB = nullptr, *hC = nullptr;
+    // pipelined host-buffer staging (tdgemm_run_host_async): two sets, a copy
+    // stream, per set an event after its copies and one after the computation
+    // that read it
+    struct HostSet {
+        void *A = nullptr, *B = nullptr, *C = nullptr;
+        cudaEvent_t copied = nullptr, done = nullptr;
+        bool used = false;
+    } hset[2];
+    cudaStream_t copy_stream = nullptr;
+    int next_set = 0;
     // Sec. 6 inner-kernel control (off: kctrl_mode == 0)
     int kctrl_mode = 0;
     double kctrl_value = 0.0, kctrl_thr = 0.0;
@@ -801,6 +811,62 @@ extern "C" tdg_status tdgemm_run_host(tdgemm_plan_t p, const void *A, const void
     return TDG_OK;
 }
 
+// pinned host memory (registered or allocated page-locked): its device alias, else nullptr
+static void *pinned_alias(const void *h) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+extern "C" tdg_status tdgemm_run_host_async(tdgemm_plan_t p, const void *A, const void *B, void *C,
+                                            double alpha, double beta, void *stream) {
+    if (!p) return fail(TDG_EINVAL, "plan is NULL");
+    if (!A || !B || !C) return fail(TDG_EINVAL, "A, B and C must be host pointers");
+    void *c_alias = pinned_alias(C);
+    if (!pinned_alias(A) || !pinned_alias(B) || !c_alias)
+        return fail(TDG_EINVAL, "tdgemm_run_host_async needs pinned host memory for A, B and C");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t esz = p->esz;
+    const size_t abytes = (size_t)((p->tA == 'N') ? p->M : p->K) * p->lda * esz;
+    const size_t bbytes = (size_t)((p->tB == 'N') ? p->K : p->N) * p->ldb * esz;
+    const size_t cbytes = (size_t)p->M * p->ldc * esz;
+    if (!p->copy_stream) {
+        CU_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        for (auto &h : p->hset) {
+            CU_TRY(cudaMalloc(&h.A, abytes));
+            CU_TRY(cudaMalloc(&h.B, bbytes));
+            CU_TRY(cudaMalloc(&h.C, cbytes));
+            CU_TRY(cudaEventCreateWithFlags(&h.copied, cudaEventDisableTiming));
+            CU_TRY(cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming));
+        }
+    }
+    // C in place over the CPU-GPU link where tdgemm_run_host writes it so
+    const bool c_direct = beta == 0.0 && (is_packed_form(p->form) || p->form == TDG_PLAIN) &&
+                          p->split_groups <= 1 && !(p->flags & TDG_PAIR_EXACT);
+    auto &h = p->hset[p->next_set];
+    p->next_set ^= 1;
+    // the set is free once the computation queued on it before has run
+    if (h.used) CU_TRY(cudaStreamWaitEvent(p->copy_stream, h.done, 0));
+    CU_TRY(cudaMemcpyAsync(h.A, A, abytes, cudaMemcpyHostToDevice, p->copy_stream));
+    CU_TRY(cudaMemcpyAsync(h.B, B, bbytes, cudaMemcpyHostToDevice, p->copy_stream));
+    if (beta != 0.0) CU_TRY(cudaMemcpyAsync(h.C, C, cbytes, cudaMemcpyHostToDevice, p->copy_stream));
+    CU_TRY(cudaEventRecord(h.copied, p->copy_stream));
+    CU_TRY(cudaStreamWaitEvent(st, h.copied, 0));
+    tdg_status r = tdgemm_run(p, h.A, h.B, c_direct ? c_alias : h.C, alpha, beta, stream);
+    if (r != TDG_OK) {
+        // the copies already queued read the caller's buffers: let them finish
+        cudaStreamSynchronize(p->copy_stream);
+        return r;
+    }
+    if (!c_direct) CU_TRY(cudaMemcpyAsync(C, h.C, cbytes, cudaMemcpyDeviceToHost, st));
+    CU_TRY(cudaEventRecord(h.done, st));
+    h.used = true;
+    return TDG_OK;
+}
+
 extern "C" tdg_status tdgemm_unpack(tdgemm_plan_t p, int64_t *rint_out, void *C, void *stream) {
     if (!p) return fail(TDG_EINVAL, "plan is NULL");
     if (!is_packed_form(p->form)) return fail(TDG_EINVAL, "unpack needs the SYM or ASYM form");
@@ -860,6 +926,14 @@ extern "C" tdg_status tdgemm_plan_destroy(tdgemm_plan_t p) {
     if (p->hA) cudaFree(p->hA);
     if (p->hB) cudaFree(p->hB);
     if (p->hC) cudaFree(p->hC);
+    for (auto &h : p->hset) {
+        if (h.A) cudaFree(h.A);
+        if (h.B) cudaFree(h.B);
+        if (h.C) cudaFree(h.C);
+        if (h.copied) cudaEventDestroy(h.copied);
+        if (h.done) cudaEventDestroy(h.done);
+    }
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->kA) cudaFree(p->kA);
     if (p->kB) cudaFree(p->kB);
     if (p->kratio) cudaFree(p->kratio);

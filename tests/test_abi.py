@@ -85,6 +85,7 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.tdgemm_quantize_pack_a(None, None, None) == 1
     assert lib.tdgemm_run(None, None, None, None, 1.0, 0.0, None) == 1
     assert lib.tdgemm_run_host(None, None, None, None, 1.0, 0.0, None) == 1
+    assert lib.tdgemm_run_host_async(None, None, None, None, 1.0, 0.0, None) == 1
     assert lib.tdgemm_plan_destroy(None) == 0
     assert lib.tdgemm_set_wait_test(None, 0) == 1
     assert lib.tdgemm_set_speedup(None, 2, 1.5) == 1

@@ -61,3 +61,49 @@ def test_run_host_matches_device(tdg, name, pinned):
     assert np.array_equal(Ch2.numpy().view(np.uint8), ref2.view(np.uint8))
     assert p.info()["device_status"] == 0
     p.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_run_host_async_pipeline_matches_device(tdg, name):
+    """Five pipelined calls on one plan and stream, inputs alternating between
+    three pinned sets and C between fresh buffers (beta = 0) and C_in with
+    alpha, beta: the copies of a call overlap the previous call's computation
+    through the plan's two staging sets; every C equals the device path's bits
+    after one synchronisation at the end."""
+    kw = dict(CASES[name])
+    M, N, K = kw.pop("M"), kw.pop("N"), kw.pop("K")
+    dt = np.float64 if kw["dtype"] == "f64" else np.float32
+    p = tdg.Plan(M, N, K, L=64, **kw)
+    sets = [(synth.uniform((M, K), 710 + i, dt), synth.uniform((K, N), 720 + i, dt)) for i in range(3)]
+    C0 = synth.uniform((M, N), 730, dt)
+    calls = [(0, 1.0, 0.0), (1, 0.5, -1.25), (2, 1.0, 0.0), (0, 0.75, 0.5), (1, 1.0, 0.0)]
+    refs = []
+    for i, alpha, beta in calls:
+        A, B = sets[i]
+        Cin = torch.from_numpy(C0).cuda()
+        refs.append(p.run(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), Cin, alpha, beta)
+                    .cpu().numpy().copy())
+    torch.cuda.synchronize()
+    hsets = [(host(A, True), host(B, True)) for A, B in sets]
+    outs = []
+    stream = torch.cuda.Stream()
+    for i, alpha, beta in calls:
+        Ch = host(C0 if beta != 0.0 else np.zeros((M, N), dt), True)
+        p.run_host_async(hsets[i][0], hsets[i][1], Ch, alpha, beta, stream=stream)
+        outs.append(Ch)
+    stream.synchronize()
+    for k, (Ch, ref) in enumerate(zip(outs, refs)):
+        assert np.array_equal(Ch.numpy().view(np.uint8), ref.view(np.uint8)), k
+    assert p.info()["device_status"] == 0
+    p.close()
+
+
+def test_run_host_async_rejects_pageable(tdg):
+    p = tdg.Plan(64, 64, 64, L=64, W=1, dtype="f32", form="plain")
+    A = torch.zeros((64, 64))
+    with pytest.raises(ValueError):
+        p.run_host_async(A, A, A)
+    from paper_1110_5765_gb300 import _lib
+    L = _lib.load()
+    assert L.tdgemm_run_host_async(p._h, A.data_ptr(), A.data_ptr(), A.data_ptr(), 1.0, 0.0, None) == 1
+    p.close()
