@@ -242,8 +242,7 @@ __global__ void __launch_bounds__(GemmCfg<T, FORM, W, BM, BN, TM, TN, BK, STAGES
     // the device planner chose another packing
     if (g.plan->W != W) return;
     // both rounding variants queued: the one the plan does not select exits
-    if constexpr (sizeof(T) == 4 && ((FORM == G_SYM && W == 2) || FORM == G_ASYM) && !KEEP &&
-                  !MIX) {
+    if constexpr (sizeof(T) == 4 && ((FORM == G_SYM && W == 2) || FORM == G_ASYM) && !KEEP) {
         if (g.small_t < 0 && small_round_ok(FORM, W, g.plan->q, g.plan->gA) != SMALL_T) return;
     }
     // this CTA's tile, row-major over ntn tiles per row; with slab splitting
@@ -681,6 +680,14 @@ cudaError_t launch_cfg(const GemmArgs<T> &g, const GemmOperands &ops, cudaStream
     if constexpr (FORM == G_SYM) {
         if (g.kmask) {
             if (g.Rbar || !ops.pa.base || !ops.pb.base) return cudaErrorInvalidValue;
+            if constexpr (sizeof(T) == 4 && W == 2) {
+                // the packed tiles' unpack rounding as for the unmixed kernel
+                if (g.small_t > 0) return launch_grid<T, FORM, W, C, false, true, true>(g, ops, st);
+                if (g.small_t < 0) {
+                    cudaError_t e = launch_grid<T, FORM, W, C, false, true, true>(g, ops, st);
+                    if (e != cudaSuccess) return e;
+                }
+            }
             return launch_grid<T, FORM, W, C, false, true>(g, ops, st);
         }
     }
