@@ -423,17 +423,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const uint32_t acc_empty_cl[2] = {cluster_addr(&acc_empty[0], 0),
                                           cluster_addr(&acc_empty[1], 0)};
         bool ok = true;
-        for (int kt = 0; kt < my_tiles && ok; ++kt) {
+        // the thread's EPI_COLS columns lie in one column block (L % 64 == 0,
+        // column groups 64-aligned), so one factor per slab, fetched a slab
+        // ahead -- across tiles too: the next tile's first factor is fetched
+        // during this tile's last slab, so the tile change costs the MMA
+        // issuer as little as possible
+        auto factor_row = [&](int k) -> const float * {
             long long m0, n0;
-            tile_origin(kt, m0, n0);
+            tile_origin(k, m0, n0);
             const long long row = m0 + quad * 32 + lane;
-            const int iblk = (int)min(row / g.L, (long long)g.nM - 1);
-            // the thread's EPI_COLS columns lie in one column block (L % 64 == 0,
-            // column groups 64-aligned), so one factor per slab, fetched a slab ahead
             const long long col0 = n0 + cgrp * EPI_COLS;
-            const int jblk = (int)min(col0 / g.L, (long long)g.nN - 1);
-            const float *prow = g.pair + (long long)iblk * g.nN + jblk;
-            float pr_next = __ldg(prow);
+            const int iblk = (int)min((long long)((unsigned long long)row / (unsigned)g.L),
+                                      (long long)g.nM - 1);
+            const int jblk = (int)min((long long)((unsigned long long)col0 / (unsigned)g.L),
+                                      (long long)g.nN - 1);
+            return g.pair + (long long)iblk * g.nN + jblk;
+        };
+        const float *prow = my_tiles > 0 ? factor_row(0) : g.pair;
+        float pr_next = my_tiles > 0 ? __ldg(prow) : 0.f;
+        for (int kt = 0; kt < my_tiles && ok; ++kt) {
+            const float *prow_n = prow;
             float cacc[EPI_COLS];
 #pragma unroll
             for (int c = 0; c < EPI_COLS; ++c) cacc[c] = 0.f;
@@ -441,7 +450,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const int gs = kt * nslab + l;
                 const int b = gs & 1;
                 const float pr = pr_next;
-                if (l + 1 < nslab) pr_next = __ldg(prow + (long long)(l + 1) * lstride);
+                if (l + 1 < nslab) {
+                    pr_next = __ldg(prow + (long long)(l + 1) * lstride);
+                } else if (kt + 1 < my_tiles) {
+                    prow_n = factor_row(kt + 1);
+                    pr_next = __ldg(prow_n);
+                }
                 if (!tc_wait_epilogue<FP8>(&acc_full[b], (gs >> 1) & 1)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t base =
@@ -478,7 +492,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             // 16 bytes) instead of 32 rows x 16 bytes
             unsigned char *stg = stg_base + ew * STG_BYTES;
             const bool vec = ((g.ldc & 3) == 0) && (((uintptr_t)g.C & 15) == 0);
+            long long m0, n0;
+            tile_origin(kt, m0, n0);
             const long long rbase = m0 + quad * 32;
+            const long long col0 = n0 + cgrp * EPI_COLS;
+            prow = prow_n;
             if (g.c_tma) {
                 // beta = 0: alpha C_acc staged in the C map's 64-byte swizzle
                 // (16-byte unit u of row r at u ^ ((r >> 1) & 3)), written by
