@@ -426,7 +426,7 @@ def run_gpu(args):
     for i in range(2):
         plan.run_host_async(host_in[i][0], host_in[i][1], host_out[i], stream=stream)
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 20))
+    e2e_steps = max(1, min(args.steps, 50))
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
     s0.record(stream)
