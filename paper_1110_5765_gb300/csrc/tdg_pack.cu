@@ -149,6 +149,10 @@ __global__ void __launch_bounds__(256) pack_k_xc_kernel(Src<T> S, int P, const D
 
 // ------------------------------------------------------------------ pack along k,
 // k contiguous in the input: 32 x-rows x 32 packed columns per tile
+// x-rows per tile of pack_k_kc_kernel (shared by the kernel and its launch)
+template <typename T, int W>
+constexpr int kc_tile() { return (sizeof(T) == 4 && W <= 2) ? 64 : 32; }
+
 template <typename T, int W>
 __global__ void __launch_bounds__(256) pack_k_kc_kernel(Src<T> S, int P, const DevPlan *plan,
                                                         int expectW, int wsign, T *out,
@@ -157,6 +161,9 @@ __global__ void __launch_bounds__(256) pack_k_kc_kernel(Src<T> S, int P, const D
     pdl_entry();
     if (expectW > 0 && plan->W != expectW) return;
     constexpr int VEC = VecT<T>::n;
+    // fp32 with W <= 2: 64 x-rows per tile (a 33 KB tile, four times the
+    // work per pass of the loop's fixed costs); else 32
+    constexpr int TILE = kc_tile<T, W>();
     constexpr int NK = TILE * W;            // k values per tile row
     constexpr int PITCH = NK + 1;
     __shared__ T s[TILE * PITCH];
@@ -725,8 +732,9 @@ cudaError_t launch_pack_k_w(const PackOperand<T> &o, const DevPlan *plan, int ex
                           expectW, out, ldo, vec_ok);
     } else {
         const int vec_ok = aligned_in && (o.sx % VEC == 0) && o.sk == 1;
-        const long long tiles = ((o.X + TILE - 1) / TILE) * ((o.K + o.L - 1) / o.L) *
-                                ((P + TILE - 1) / TILE);
+        constexpr int TK = kc_tile<T, W>();
+        const long long tiles = ((o.X + TK - 1) / TK) * ((o.K + o.L - 1) / o.L) *
+                                ((P + TK - 1) / TK);
         return launch_pdl(pack_k_kc_kernel<T, W>,
                           dim3(resident_grid((const void *)pack_k_kc_kernel<T, W>, tiles, 4)),
                           dim3(256), 0, st, S, P, plan, expectW, wsign, out, ldo, rows_out,
