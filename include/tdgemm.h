@@ -323,8 +323,8 @@ tdg_status tdgemm_snr(const void *C, int64_t ldc, tdg_dtype dtype, const double 
  * previous call's contents; each call clears what must start at zero), so
  * calls whose device work overlaps — different streams, or threads sharing a
  * device — race: order them on one stream.  The first call on a device looks
- * up the array's device address (with that device current); make it before
- * any stream capture begins.  The paper has no counterpart to this entry point.
+ * up the array's device address (with that device current) and caches it.
+ * The paper has no counterpart to this entry point.
  */
 tdg_status tdgemm_run_static(char transA, char transB, int64_t M, int64_t N, int64_t K,
                              int64_t lda, int64_t ldb, int64_t ldc, int L, int W,

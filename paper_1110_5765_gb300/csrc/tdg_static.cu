@@ -24,8 +24,7 @@
 //     work overlaps (different streams, or different host threads on one
 //     device) race on the array: order them on one stream.
 //   * The first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress, with that device current) and caches it; make
-//     that first call before any stream capture begins.
+//     (cudaGetSymbolAddress, with that device current) and caches it.
 // The paper has no counterpart to this entry point.
 #include <cuda.h>
 #include <cuda_runtime.h>
