@@ -619,8 +619,9 @@ ROOFLINE_FORMS = [
 
 
 def rooflines(forms: dict, pk: dict) -> dict:
-    """Per-form rooflines of the spec comparison (4096^3 uniform, 8192^3
-    Laplacian; 40 dB targets, 20 dB where fp32 packing engages)."""
+    """Per-form rooflines of every form beside the conventional products
+    (4096^3 uniform, 8192^3 Laplacian; 40 dB targets, 20 dB where fp32 packing
+    engages)."""
     out = {"_": ("T: whole-path effective TFLOP/s (2MNK/t); dB: SNR vs fp64; W: packing used; "
                  "kT: GEMM kernel algorithmic TFLOP/s (2 per FMA it performs); f = kT / peak; "
                  f"pk: f32 = {pk['f32_tflops']:.1f}, f64 = {pk['f64_tflops']:.2f} TFLOP/s "
@@ -1019,7 +1020,7 @@ def pca2d_study(out_path=None):
 
 
 def mlp_study(out_path=None, steps=50):
-    """Config 4, the differentiation form: a 128-1024-1024-10 tanh MLP, batch
+    """The differentiation form: a 128-1024-1024-10 tanh MLP, batch
     4096, synthetic labels from a teacher MLP, cross-entropy, SGD lr 0.1.  Every
     GEMM (3 forward, 5 adjoint products per step) through the straight-through
     autograd form at a 20 dB target (RMS-scaled noise), beside the same
@@ -1173,8 +1174,8 @@ def reuse_study(out_path=None):
     packed form, so each call companders and packs only A.  Whole-path time of
     a full pack + GEMM against an A-only pack + GEMM (L2 flushed before each
     call, median of 20), with the reused result checked bit for bit against
-    the full one; at 4096^3 (uniform inputs) and for the forward pass of the
-    config-4 MLP (batch 4096, 128 -> 1024 -> 1024 -> 10, ReLU) with fixed
+    the full one; at 4096^3 (uniform inputs) and for the forward pass of a
+    128 -> 1024 -> 1024 -> 10 MLP (batch 4096, ReLU between layers) with fixed
     weights."""
     import torch
     from paper_1110_5765_gb300 import build as b
@@ -1360,7 +1361,8 @@ def main():
     ap.add_argument("--pairx", default=None, metavar="OUT.json",
                     help="pair-exact against separable companders at 4096^3")
     ap.add_argument("--mlp", default=None, metavar="OUT.json",
-                    help="time MLP training through the autograd form (config 4)")
+                    help="time training of a 128-1024-1024-10 MLP (batch 4096) through the "
+                         "autograd form")
     ap.add_argument("--pca2d", default=None, metavar="OUT.json",
                     help="run the 2DPCA face-recognition study (Sec. 8.A, Table 1)")
     ap.add_argument("--reuse", default=None, metavar="OUT.json",

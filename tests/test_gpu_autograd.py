@@ -125,8 +125,8 @@ def test_mlp_training_50_steps(ag):
 
 
 @pytest.mark.parametrize("target", [20.0, 30.0])
-def test_config4_mlp_gradients_every_layer(ag, target):
-    """Config 4's MLP (128-1024-1024-10, tanh, batch 4096, synthetic teacher
+def test_mlp_128_1024_1024_10_gradients_every_layer(ag, target):
+    """The 128-1024-1024-10 MLP (tanh, batch 4096, synthetic teacher
     labels, cross-entropy) at the student's initial weights: every layer's dW
     from the companded-and-packed forward and adjoint products (fp32, sym,
     W = 2, distortion target ``target``) against

@@ -65,9 +65,9 @@ def same_bits(a, b):
     return np.array_equal(np.asarray(a).view(np.uint8), np.asarray(b).view(np.uint8))
 
 
-# ------------------------------------------------------------------ config 1
+# ------------------------------------------------- 256^3 fp64, 8 bits, W = 2
 @pytest.mark.parametrize("form", ["sym", "asym"])
-def test_config1_bitexact(tdg, orc, form):
+def test_256_fp64_8bit_w2_bitexact(tdg, orc, form):
     """256^3 fp64 Gaussian, L = 64, 8-bit companding, W = 2: integers and C
     bit-identical to the oracle; plan identical."""
     A = synth.gaussian((256, 256), 1111)

@@ -170,7 +170,7 @@ def test_headroom_extreme_inputs(orc, dtype, W, form):
 
 
 # ---------------------------------------------------------------- Prop. 2 / eq. 21
-def test_config1_bitexact_and_model(orc):
+def test_256_fp64_8bit_w2_bitexact_and_model(orc):
     """256^3 fp64, L = 64, 8-bit companding, W = 2: inside headroom, so the
     unpacked integers equal the per-slab integer products for both forms, and
     the measured SNR agrees with eq. 19/20 (Fig. 4's agreement) within 0.3 dB."""
