@@ -331,3 +331,67 @@ def test_few_tiles_many_slabs(tdg, orc, dtype, form):
     g = run_gpu(tdg, A, B, L=128, W=W, dtype=dtype, form=form, bits=7, alpha=0.75, beta=-1.5,
                 Cin=Cin)
     assert same_bits(g["C"], ref.C)
+
+
+# ------------------------------------------------------------------ all-zero blocks
+def _run_target(tdg, orc, A, B, *, L, W, dtype, form, target):
+    """Target mode on both sides with the same made-up s(R) table."""
+    st, dense = _synthetic_table(orc, dtype, form, L, W)
+    ref = orc.tdgemm(A, B, L=L, W=W, dtype=dtype, form=form, target_db=target, s_table=st)
+    M, K = A.shape
+    N = B.shape[1]
+    p = tdg.Plan(M, N, K, L=L, W=W, dtype=dtype, form=form, target_snr_db=target, rep_noise=None)
+    for w in range(2, W + 1):
+        p.set_rep_noise(w, dense[w], 0)
+    C = torch.zeros((M, N), dtype=TT[dtype], device="cuda")
+    p.run(dev(A), dev(B), C)
+    i = p.info()
+    assert i["device_status"] == 0, i
+    assert i["W_used"] == ref.plan.W
+    if ref.plan.W > 1:
+        assert (i["q"], i["gamma_a"], i["gamma_b"], i["level"]) == \
+            (ref.plan.q, ref.plan.gA, ref.plan.gB, ref.plan.t)
+        if math.isinf(ref.plan.pred_snr_db):
+            assert i["pred_snr_db"] == ref.plan.pred_snr_db
+        else:
+            assert abs(i["pred_snr_db"] - ref.plan.pred_snr_db) < 1e-6
+    return C.cpu().numpy(), ref
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("form", ["sym", "asym"])
+@pytest.mark.parametrize("mode", ["bits", "target"])
+def test_zero_blocks(tdg, orc, dtype, form, mode):
+    """All-zero blocks (c = s = 0): a slab of A zero in every row block and a
+    zero column panel of B, ragged M, K, N; fixed bits at W = 2 and 3, and
+    target mode: C (and the plan) bit-identical to the oracle, the zero panel
+    exactly 0."""
+    L = 64
+    T = NP[dtype]
+    A = synth.gaussian((3 * L + 5, 5 * L + 9), 1401, T)
+    B = synth.laplace((5 * L + 9, 2 * L + 7), 1402, T)
+    A[:, 2 * L:3 * L] = 0
+    B[:, L:2 * L] = 0
+    if mode == "bits":
+        for W in (2, 3):
+            ref = orc.tdgemm(A, B, L=L, W=W, dtype=dtype, form=form, bits=7)
+            g = run_gpu(tdg, A, B, L=L, W=W, dtype=dtype, form=form, bits=7)
+            assert same_bits(g["C"], ref.C), W
+            assert np.all(g["C"][:, L:2 * L] == 0)
+    else:
+        C, ref = _run_target(tdg, orc, A, B, L=L, W=3, dtype=dtype, form=form, target=20.0)
+        assert ref.plan.W >= 2
+        assert same_bits(C, ref.C)
+        assert np.all(C[:, L:2 * L] == 0)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_zero_operand_target_mode(tdg, orc, dtype):
+    """A = 0: the model's noise and signal vanish (predicted SNR infinite), so
+    both planners keep the requested W at the lowest R_max level; C = 0."""
+    L = 64
+    A = np.zeros((2 * L + 3, 3 * L), NP[dtype])
+    B = synth.gaussian((3 * L, 2 * L), 1403, NP[dtype])
+    C, ref = _run_target(tdg, orc, A, B, L=L, W=3, dtype=dtype, form="sym", target=30.0)
+    assert ref.plan.W == 3 and math.isinf(ref.plan.pred_snr_db)
+    assert same_bits(C, ref.C) and np.all(C == 0)

@@ -256,3 +256,29 @@ def test_tc_int_output_paths_alpha_beta_ldc(tdg, orc, L):
         assert same_bits(got[:, :N], want), (beta, ldc)
         if ldc > N:
             assert same_bits(got[:, N:], Cin[:, N:]), "padding column written"
+
+
+@pytest.mark.parametrize("form,bits,target", [("tc_int", 8, math.nan), ("tc_int", 0, 40.0),
+                                              ("tc_fp8", 0, math.nan)])
+def test_tc_zero_blocks(tdg, orc, form, bits, target):
+    """All-zero blocks (c = s = 0) on the tensor-core forms: a slab of A zero
+    in every row block and a zero column panel of B, ragged M, K, N (both
+    the k-contiguous A and the x-contiguous B path of the code kernels): the
+    integer form bit-exact, E4M3 within the fp32-summation bound; the zero
+    panel exactly 0."""
+    L = 128
+    A = synth.laplace((300, 5 * L + 40), 1411, np.float32)
+    B = synth.gaussian((5 * L + 40, 2 * L + 30), 1412, np.float32)
+    A[:, 2 * L:3 * L] = 0
+    B[:, L:2 * L] = 0
+    if form == "tc_int":
+        ref = orc.tc_int_gemm(A, B, L=L, bits=bits)
+        C, info = run_tc(tdg, A, B, form=form, bits=bits, target=target)
+        assert (info["gamma_a"], info["gamma_b"]) == (ref.plan.gA, ref.plan.gB)
+        assert same_bits(C, ref.C)
+    else:
+        ref = orc.tc_fp8_gemm(A, B, L=L)
+        C, _ = run_tc(tdg, A, B, form=form)
+        bound = _fp8_bound(orc, A, B, ref, (0, A.shape[0]), (0, B.shape[1]), L)
+        assert np.all(np.abs(C.astype(np.float64) - ref.C) <= bound + 1e-30)
+    assert np.all(C[:, L:2 * L] == 0)

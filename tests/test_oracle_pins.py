@@ -713,3 +713,61 @@ def test_pair_exact_beats_separable_on_unlike_blocks(orc):
     px = orc.tdgemm_pair_exact(A, B, L=L, W=2, dtype="f64", plan=sep.plan)
     assert sep.plan.W <= sep.plan.Wef
     assert orc.snr_db(px, ref) > orc.snr_db(sep.C, ref) + 0.1
+
+
+# ------------------------------------------------------------------ all-zero blocks (R12)
+def _zero_slab_and_panel(A, B, L, slab, panel):
+    A = A.copy()
+    B = B.copy()
+    A[:, slab * L:(slab + 1) * L] = 0.0
+    B[:, panel * L:(panel + 1) * L] = 0.0
+    return A, B
+
+
+def _drop_slab(A, B, L, slab):
+    keep = np.r_[0:slab * L, (slab + 1) * L:A.shape[1]]
+    return np.ascontiguousarray(A[:, keep]), np.ascontiguousarray(B[keep, :])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("form", ["sym", "asym"])
+@pytest.mark.parametrize("mode", ["bits", "target"])
+def test_zero_blocks_contribute_nothing(orc, dtype, form, mode):
+    """An all-zero block gets c = s = 0 and adds exactly zero (eqs. 3, 5 and 2
+    with c = 0): a slab of A that is zero everywhere leaves C as the product
+    with that slab removed from K (same plan: the zero slab adds nothing to
+    the model's sums), and a zero column panel of B gives outputs exactly 0."""
+    L = 64
+    T = np.float64 if dtype == "f64" else np.float32
+    A = synth.gaussian((3 * L + 5, 5 * L), 1401, T)
+    B = synth.laplace((5 * L, 2 * L + 7), 1402, T)
+    A, B = _zero_slab_and_panel(A, B, L, slab=2, panel=1)
+    A2, B2 = _drop_slab(A, B, L, slab=2)
+    kw = dict(L=L, W=2, dtype=dtype, form=form)
+    if mode == "bits":
+        kw["bits"] = 7
+    else:
+        kw.update(target_db=20.0, s_table=orc.load_s_table())
+    r = orc.tdgemm(A, B, **kw)
+    r2 = orc.tdgemm(A2, B2, **kw)
+    assert (r.plan.W, r.plan.q, r.plan.gA, r.plan.gB) == (r2.plan.W, r2.plan.q, r2.plan.gA, r2.plan.gB)
+    if mode == "target":
+        assert r.plan.W == 2 and r.plan.pred_snr_db == r2.plan.pred_snr_db
+    assert np.all(r.cA[:, 2] == 0) and np.all(r.sA[:, 2] == 0)
+    assert np.all(r.cB[:, 1] == 0) and np.all(r.sB[:, 1] == 0)
+    assert np.array_equal(r.C, r2.C)
+    assert np.all(r.C[:, L:2 * L] == 0)
+    assert np.count_nonzero(r.C[:, :L]) == r.C[:, :L].size
+
+
+def test_zero_operand_target_mode(orc):
+    """A = 0: every model term vanishes (N = 0, predicted SNR infinite), so the
+    requested packing is kept at the lowest R_max level and C is exactly 0."""
+    L = 64
+    A = np.zeros((2 * L, 3 * L), np.float32)
+    B = synth.gaussian((3 * L, 2 * L), 1403, np.float32)
+    r = orc.tdgemm(A, B, L=L, W=2, dtype="f32", form="sym", target_db=30.0,
+                   s_table=orc.load_s_table())
+    assert r.plan.W == 2 and r.plan.pred_snr_db == math.inf
+    assert r.plan.t == min(t for t in range(200) if orc.r_level(t) >= L)
+    assert np.all(r.C == 0) and not np.any(np.signbit(r.C))
