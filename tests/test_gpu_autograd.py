@@ -115,7 +115,7 @@ def test_mlp_training_50_steps(ag):
             with torch.no_grad():
                 for w in ws:
                     w -= 0.1 * w.grad
-            losses.append(float(loss))
+            losses.append(float(loss.detach()))
         return losses
 
     ref = train(False)
