@@ -36,7 +36,9 @@
 //               C_acc = fma(r, s_A s_B, C_acc) in fp32 and releases the
 //               accumulator to the even CTA's MMA issuer, so the
 //               next-but-one slab's MMAs can reuse it while this one is
-//               being promoted.
+//               being promoted.  At a tile's end each warp writes its
+//               32 x 64 block of C through a 2 KB staging tile: TMA stores
+//               when beta = 0 and C is mappable, else coalesced stores.
 // Every wait is bounded (2 s of global time); on expiry the CTA records
 // TDG_ETIMEOUT, drains what it issued (bounded) and frees its TMEM.
 #include <cuda_fp16.h>
