@@ -11,12 +11,17 @@
 //                  unpacked operands and the plain copies):
 //                    - x contiguous in the input: 16-byte vector loads of the
 //                      W digit rows, vector stores, no shared memory;
-//                    - k contiguous in the input: a 32 x 32W tile staged in
+//                    - k contiguous in the input: a TILE x TILE W tile (TILE =
+//                      64 x-rows for fp32 with W <= 2, else 32) staged in
 //                      shared memory with vector loads, then written along x.
 //   pack along x   out[k][i P + j]  (eq. 11, asymmetric A), tile staged in
 //                  shared memory.
 //   k-major codes  out[x][k] (tensor-core forms): integer-valued fp16, or E4M3
 //                  (round to nearest even, saturating).
+//   fused codes    for companders that depend on their own block only (fixed
+//                  bits, E4M3) and L <= 128: one 512-thread CTA per block
+//                  reads it once into registers, reduces max|x| and sum x^2,
+//                  writes c and s and encodes the codes.
 // P = ceil(L / W) packed numbers per block.  Each kernel first reads the
 // device plan and returns unless the planner chose its packing; the grids are
 // capped and loop over tiles so that such early exits cost little.
@@ -148,8 +153,8 @@ __global__ void __launch_bounds__(256) pack_k_xc_kernel(Src<T> S, int P, const D
 }
 
 // ------------------------------------------------------------------ pack along k,
-// k contiguous in the input: 32 x-rows x 32 packed columns per tile
-// x-rows per tile of pack_k_kc_kernel (shared by the kernel and its launch)
+// k contiguous in the input: x-rows per tile of pack_k_kc_kernel (shared by
+// the kernel and its launch), each tile TILE packed columns wide
 template <typename T, int W>
 constexpr int kc_tile() { return (sizeof(T) == 4 && W <= 2) ? 64 : 32; }
 
