@@ -557,11 +557,12 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
             if (!tc_fused) {       // (the fused path wrote the codes with the statistics)
                 const long long ldk = round_up(p->K, 128);
                 const int fp8 = p->form == TDG_TC_FP8;
-                CU_TRY(launch_codes(operand_A<float>(p, A, (const float *)p->cA), fp8, p->Abuf,
-                                    ldk, st));
+                // B first, as for the packs: its blocks were read last
                 if (!reuse_b)
                     CU_TRY(launch_codes(operand_B<float>(p, B, (const float *)p->cB), fp8,
                                         p->Bbuf, ldk, st));
+                CU_TRY(launch_codes(operand_A<float>(p, A, (const float *)p->cA), fp8, p->Abuf,
+                                    ldk, st));
             }
         }
     } else {
@@ -582,17 +583,19 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
             } else if (px) {
                 // each CTA compands and packs its own tiles from A and B
             } else if (p->form == TDG_SYM) {
-                CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w, -1,
-                                        (T *)p->Abuf, s.a_ld, s.a_rows, st));                   // eq. 6
+                // B first: the statistics pass read B's blocks last, so they
+                // are still in L2
                 if (!reuse_b)
                     CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, (const T *)p->cB), w, p->dplan, w,
                                             +1, (T *)p->Bbuf, s.b_ld, s.b_rows, st));      // eq. 7
+                CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w, -1,
+                                        (T *)p->Abuf, s.a_ld, s.a_rows, st));                   // eq. 6
             } else {
-                CU_TRY(launch_pack_x<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w, -1,
-                                        (T *)p->Abuf, s.a_ld, st));                   // eq. 11
                 if (!reuse_b)
                     CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, (const T *)p->cB), 1, p->dplan, w,
                                             0, (T *)p->Bbuf, s.b_ld, s.b_rows, st));       // b~ only
+                CU_TRY(launch_pack_x<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w, -1,
+                                        (T *)p->Abuf, s.a_ld, st));                   // eq. 11
             }
         }
     }
