@@ -13,6 +13,7 @@
 
 #include "tdg_common.cuh"
 #include "tdg_internal.h"
+#include "tdg_pack.h"
 #include "tdgemm.h"
 
 using namespace tdg;
@@ -583,13 +584,14 @@ static tdg_status pack_impl(tdgemm_plan_t p, const T *A, const T *B, cudaStream_
             } else if (px) {
                 // each CTA compands and packs its own tiles from A and B
             } else if (p->form == TDG_SYM) {
-                // B first: the statistics pass read B's blocks last, so they
-                // are still in L2
                 if (!reuse_b)
-                    CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, (const T *)p->cB), w, p->dplan, w,
-                                            +1, (T *)p->Bbuf, s.b_ld, s.b_rows, st));      // eq. 7
-                CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w, -1,
-                                        (T *)p->Abuf, s.a_ld, s.a_rows, st));                   // eq. 6
+                    CU_TRY(launch_pack_k_pair<T>(operand_A<T>(p, A, (const T *)p->cA),
+                                                 operand_B<T>(p, B, (const T *)p->cB), w,
+                                                 p->dplan, w, (T *)p->Abuf, s.a_ld, s.a_rows,
+                                                 (T *)p->Bbuf, s.b_ld, s.b_rows, st));   // eqs. 6, 7
+                else
+                    CU_TRY(launch_pack_k<T>(operand_A<T>(p, A, (const T *)p->cA), w, p->dplan, w,
+                                            -1, (T *)p->Abuf, s.a_ld, s.a_rows, st));   // eq. 6
             } else {
                 if (!reuse_b)
                     CU_TRY(launch_pack_k<T>(operand_B<T>(p, B, (const T *)p->cB), 1, p->dplan, w,

@@ -32,6 +32,7 @@
 
 #include "tdg_common.cuh"
 #include "tdg_internal.h"
+#include "tdg_pack.h"
 
 namespace tdg {
 
@@ -97,21 +98,17 @@ __device__ inline void vstore(T *p, const T *o) {
 
 // ------------------------------------------------------------------ pack along k,
 // x contiguous in the input: one item = VEC consecutive x of one packed row
+// (the loop of CTA vb of vg working on this operand)
 template <typename T, int W>
-__global__ void __launch_bounds__(256) pack_k_xc_kernel(Src<T> S, int P, const DevPlan *plan,
-                                                        int expectW, int wsign, T *out,
-                                                        long long ldo, long long rows_out,
-                                                        int vec_ok) {
-    pdl_entry();
-    if (expectW > 0 && plan->W != expectW) return;
+__device__ __forceinline__ void pack_k_xc_body(const Src<T> &S, int P, T w, T *out, long long ldo,
+                                               long long rows_out, int vec_ok, long long vb,
+                                               long long vg) {
     constexpr int VEC = VecT<T>::n;
-    const T w = W > 1 ? pack_weight<T>(plan, wsign) : T(1);
     const bool compand = S.c != nullptr;
     const int L = S.L;
     const long long nx = (S.X + VEC - 1) / VEC;
     const long long items = rows_out * nx;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
-         it += (long long)gridDim.x * blockDim.x) {
+    for (long long it = vb * blockDim.x + threadIdx.x; it < items; it += vg * blockDim.x) {
         const long long row = it / nx;                 // l * P + j
         const long long x = (it - row * nx) * VEC;
         const int l = (int)(row / P), j = (int)(row - (long long)l * P);
@@ -152,6 +149,17 @@ __global__ void __launch_bounds__(256) pack_k_xc_kernel(Src<T> S, int P, const D
     }
 }
 
+template <typename T, int W>
+__global__ void __launch_bounds__(256) pack_k_xc_kernel(Src<T> S, int P, const DevPlan *plan,
+                                                        int expectW, int wsign, T *out,
+                                                        long long ldo, long long rows_out,
+                                                        int vec_ok) {
+    pdl_entry();
+    if (expectW > 0 && plan->W != expectW) return;
+    const T w = W > 1 ? pack_weight<T>(plan, wsign) : T(1);
+    pack_k_xc_body<T, W>(S, P, w, out, ldo, rows_out, vec_ok, blockIdx.x, gridDim.x);
+}
+
 // ------------------------------------------------------------------ pack along k,
 // k contiguous in the input: x-rows per tile of pack_k_kc_kernel (shared by
 // the kernel and its launch), each tile TILE packed columns wide
@@ -159,12 +167,9 @@ template <typename T, int W>
 constexpr int kc_tile() { return (sizeof(T) == 4 && W <= 2) ? 64 : 32; }
 
 template <typename T, int W>
-__global__ void __launch_bounds__(256) pack_k_kc_kernel(Src<T> S, int P, const DevPlan *plan,
-                                                        int expectW, int wsign, T *out,
-                                                        long long ldo, long long rows_out,
-                                                        int vec_ok) {
-    pdl_entry();
-    if (expectW > 0 && plan->W != expectW) return;
+__device__ __forceinline__ void pack_k_kc_body(const Src<T> &S, int P, T w, T *out, long long ldo,
+                                               long long rows_out, int vec_ok, long long vb,
+                                               long long vg) {
     constexpr int VEC = VecT<T>::n;
     // fp32 with W <= 2: 64 x-rows per tile (a 33 KB tile, four times the
     // work per pass of the loop's fixed costs); else 32
@@ -173,14 +178,13 @@ __global__ void __launch_bounds__(256) pack_k_kc_kernel(Src<T> S, int P, const D
     constexpr int PITCH = NK + 1;
     __shared__ T s[TILE * PITCH];
     __shared__ T crow[TILE];
-    const T w = W > 1 ? pack_weight<T>(plan, wsign) : T(1);
     const bool compand = S.c != nullptr;
     const int L = S.L;
     const int jt = (P + TILE - 1) / TILE;
     const long long xt = (S.X + TILE - 1) / TILE;
     const int nK = (int)((S.K + L - 1) / L);
     const long long tiles = xt * nK * jt;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (long long t = vb; t < tiles; t += vg) {
         const long long xtile = t % xt;
         const long long r = t / xt;
         const int l = (int)(r / jt), j0 = (int)(r % jt) * TILE;
@@ -226,6 +230,50 @@ __global__ void __launch_bounds__(256) pack_k_kc_kernel(Src<T> S, int P, const D
             for (int i = W - 2; i >= 0; --i) acc = fma_t(w, acc, d[i]);
             out[row * ldo + x] = acc;
         }
+    }
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(256) pack_k_kc_kernel(Src<T> S, int P, const DevPlan *plan,
+                                                        int expectW, int wsign, T *out,
+                                                        long long ldo, long long rows_out,
+                                                        int vec_ok) {
+    pdl_entry();
+    if (expectW > 0 && plan->W != expectW) return;
+    const T w = W > 1 ? pack_weight<T>(plan, wsign) : T(1);
+    pack_k_kc_body<T, W>(S, P, w, out, ldo, rows_out, vec_ok, blockIdx.x, gridDim.x);
+}
+
+// Both operands of the symmetric form in one launch, A k-contiguous (eq. 6)
+// and B x-contiguous (eq. 7), the layouts of C = A B with row-major A and B:
+// the first 2 m CTAs alternate between the two (m = the smaller CTA count),
+// the rest go to the operand with more, so every SM runs both kinds at once
+// (the A pack is issue-bound, the B pack latency-bound).
+template <typename T, int W>
+__global__ void __launch_bounds__(256) pack_k_pair_kernel(Src<T> SA, Src<T> SB, int P,
+                                                          const DevPlan *plan, int expectW,
+                                                          T *outA, long long ldoA,
+                                                          long long rowsA, int vecA, T *outB,
+                                                          long long ldoB, long long rowsB,
+                                                          int vecB, long long gA, long long gB) {
+    pdl_entry();
+    if (expectW > 0 && plan->W != expectW) return;
+    const long long b = blockIdx.x, m = min(gA, gB);
+    bool isA;
+    long long vb;
+    if (b < 2 * m) {
+        isA = (b & 1) != 0;
+        vb = b >> 1;
+    } else {
+        isA = gA > gB;
+        vb = m + (b - 2 * m);
+    }
+    if (isA) {
+        const T w = W > 1 ? pack_weight<T>(plan, -1) : T(1);
+        pack_k_kc_body<T, W>(SA, P, w, outA, ldoA, rowsA, vecA, vb, gA);
+    } else {
+        const T w = W > 1 ? pack_weight<T>(plan, +1) : T(1);
+        pack_k_xc_body<T, W>(SB, P, w, outB, ldoB, rowsB, vecB, vb, gB);
     }
 }
 
@@ -762,6 +810,51 @@ cudaError_t launch_pack_x_w(const PackOperand<T> &o, const DevPlan *plan, int ex
 
 }  // namespace
 
+// The symmetric form's two packs (A with wsign -1, B with +1): one launch of
+// pack_k_pair_kernel when A is k-contiguous and B x-contiguous, else B's pack
+// and then A's.
+template <typename T, int W>
+cudaError_t launch_pack_k_pair_w(const PackOperand<T> &a, const PackOperand<T> &b,
+                                 const DevPlan *plan, int expectW, T *outA, long long ldoA,
+                                 long long rowsA, T *outB, long long ldoB, long long rowsB,
+                                 cudaStream_t st) {
+    constexpr int VEC = VecT<T>::n;
+    const bool a_copy = W == 1 && a.c == nullptr && a.sk == 1 && rowsA == a.K;
+    if (a.sx == 1 || a_copy || b.sx != 1) {
+        cudaError_t e = launch_pack_k_w<T, W>(b, plan, expectW, +1, outB, ldoB, rowsB, st);
+        if (e != cudaSuccess) return e;
+        return launch_pack_k_w<T, W>(a, plan, expectW, -1, outA, ldoA, rowsA, st);
+    }
+    Src<T> SA = make_src(a), SB = make_src(b);
+    const int P = (a.L + W - 1) / W;
+    const int vecA = ((uintptr_t)a.src % 16 == 0) && (a.sx % VEC == 0) && a.sk == 1;
+    const int vecB = ((uintptr_t)b.src % 16 == 0) && ((uintptr_t)outB % 16 == 0) &&
+                     (ldoB % VEC == 0) && (b.sk % VEC == 0);
+    constexpr int TK = kc_tile<T, W>();
+    const long long tilesA = ((a.X + TK - 1) / TK) * ((a.K + a.L - 1) / a.L) * ((P + TK - 1) / TK);
+    const long long blocksB = (rowsB * ((b.X + VEC - 1) / VEC) + 255) / 256;
+    const void *kern = (const void *)pack_k_pair_kernel<T, W>;
+    const long long gA = resident_grid(kern, tilesA, 2);
+    const long long gB = resident_grid(kern, blocksB, 2);
+    return launch_pdl(pack_k_pair_kernel<T, W>, dim3((unsigned)(gA + gB)), dim3(256), 0, st, SA,
+                      SB, P, plan, expectW, outA, ldoA, rowsA, vecA, outB, ldoB, rowsB, vecB,
+                      gA, gB);
+}
+
+template <typename T>
+cudaError_t launch_pack_k_pair(const PackOperand<T> &a, const PackOperand<T> &b, int W,
+                               const DevPlan *plan, int expectW, T *outA, long long ldoA,
+                               long long rowsA, T *outB, long long ldoB, long long rowsB,
+                               cudaStream_t st) {
+    switch (W) {
+        case 1: return launch_pack_k_pair_w<T, 1>(a, b, plan, expectW, outA, ldoA, rowsA, outB, ldoB, rowsB, st);
+        case 2: return launch_pack_k_pair_w<T, 2>(a, b, plan, expectW, outA, ldoA, rowsA, outB, ldoB, rowsB, st);
+        case 3: return launch_pack_k_pair_w<T, 3>(a, b, plan, expectW, outA, ldoA, rowsA, outB, ldoB, rowsB, st);
+        case 4: return launch_pack_k_pair_w<T, 4>(a, b, plan, expectW, outA, ldoA, rowsA, outB, ldoB, rowsB, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t launch_pack_k(const PackOperand<T> &o, int W, const DevPlan *plan, int expectW,
                           int wsign, T *out, long long ldo, long long rows_out, cudaStream_t st) {
@@ -848,6 +941,15 @@ cudaError_t launch_codes_stats(const PackOperand<float> &a, double *mxA, double 
                       gamma, ldo, plan);
 }
 
+template cudaError_t launch_pack_k_pair<float>(const PackOperand<float> &, const PackOperand<float> &,
+                                               int, const DevPlan *, int, float *, long long,
+                                               long long, float *, long long, long long,
+                                               cudaStream_t);
+template cudaError_t launch_pack_k_pair<double>(const PackOperand<double> &,
+                                                const PackOperand<double> &, int,
+                                                const DevPlan *, int, double *, long long,
+                                                long long, double *, long long, long long,
+                                                cudaStream_t);
 template cudaError_t launch_pack_k<float>(const PackOperand<float> &, int, const DevPlan *, int, int,
                                           float *, long long, long long, cudaStream_t);
 template cudaError_t launch_pack_k<double>(const PackOperand<double> &, int, const DevPlan *, int,
