@@ -325,13 +325,13 @@ def launches_per_step(plan) -> int:
     """Kernels this library queues per tdgemm_run for a target-mode symmetric
     fp32 plan with fallback, inputs 'N'/'N': block statistics of A and B (one
     launch), planner (per-slab aggregates; every candidate level, the last CTA
-    deciding the plan), companders and de-companding factors, pack A and B for
-    W = 2, plain copy of A for the W = 1 fallback (B is used in place), the
-    packed GEMM for W = 2 in both rounding variants of eq. 10 (the add-subtract
-    one when the planned q allows it, the rintf one otherwise) and the plain
-    GEMM for the fallback (kernels not chosen by the planner exit at entry).
-    Counted from the ncu launch list of one step."""
-    return 1 + 2 + 2 + 2 + 1 + 3
+    deciding the plan), companders and de-companding factors, the packs of A
+    and B for W = 2 (one launch), plain copy of A for the W = 1 fallback (B is
+    used in place), the packed GEMM for W = 2 in both rounding variants of
+    eq. 10 (the add-subtract one when the planned q allows it, the rintf one
+    otherwise) and the plain GEMM for the fallback (kernels not chosen by the
+    planner exit at entry).  Counted from the ncu launch list of one step."""
+    return 1 + 2 + 2 + 1 + 1 + 3
 
 
 def run_gpu(args):
